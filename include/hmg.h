@@ -1,0 +1,222 @@
+/*
+ * hmg -- FFT-based (Eyre-Milton accelerated) thermal homogenization of coated-sphere
+ * composites on one NVIDIA GB300.  C ABI of libhmg.so.
+ *
+ * The method is that of Lemaitre, Salnikov, Choi & Karamian, "Computation of thermal
+ * properties via 3D homogenization of multiphase materials using FFT-based
+ * accelerated scheme" (arXiv:1504.07499):
+ *   - §2 / Fig. 1: identical non-overlapping spheres (centre, outer radius r_s), each
+ *     with a coating of width l * r_s (0 < l < 1); three phases: matrix (0),
+ *     inclusion core (1), coating shell (2); isotropic conductivities k I (§2, §5).
+ *   - §3, eq. 1-3: periodic cell problem in polarization form with a constant
+ *     reference medium L0 = -k0 I, k0 = sqrt(min k * max k) (§5), and the Green
+ *     operator Gamma0(xi) = xi xi^T / (xi . L0 xi), Gamma0(0) = 0.
+ *   - §3 Algorithm, steps 1-7: the accelerated iteration and its two-stage
+ *     convergence test (eps_comp, then eps_eq).
+ *   - §3 last paragraph: <phi> = -L_hom grad Theta gives the 3x3 effective tensor.
+ *
+ * Conventions shared by every call
+ *   - Grids are N x N x N voxels stored z-major, x fastest: index (z*N + y)*N + x.
+ *     N must be even, N = 2 * 2^a * 3^b, 8 <= N <= 512.
+ *   - Phase ids: 0 matrix, 1 inclusion, 2 coating (uint8 per voxel).
+ *   - Vector fields hold components x, y, z as three consecutive N^3 blocks.
+ *   - A pointer argument may be host memory or device memory of the context's GPU;
+ *     the library detects which and copies as needed.  All buffers are owned by the
+ *     caller and are only read (inputs) or written (outputs) during the call.
+ *   - Every call returns an hmg_status; nothing aborts, throws or traps.  On error
+ *     hmg_last_error() describes the failure (thread-local, valid until the next call).
+ *   - A context is not thread-safe: serialize calls on one context.
+ *   - Wavevectors are xi_j = 2 pi m_j / N with m_j in (-N/2, N/2].  Nyquist components
+ *     (m_j = N/2) are dropped from xi except in a mode whose only nonzero component is
+ *     a Nyquist one; Gamma0 is zero where the resulting xi is zero.
+ */
+#ifndef HMG_H
+#define HMG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hmg_ctx hmg_ctx;
+
+/* One coated sphere (§2): centre in the periodic unit cube, r = OUTER radius r_s. */
+typedef struct {
+    double cx, cy, cz, r;
+} hmg_sphere;
+
+typedef enum {
+    HMG_OK = 0,
+    HMG_PENDING = 1,          /* hmg_poll: request not finished yet */
+    HMG_INVALID_ARG = -1,     /* bad size, value or pointer; nothing was launched */
+    HMG_OUT_OF_MEMORY = -2,   /* device allocation failed or the HBM budget is exceeded */
+    HMG_NOT_CONVERGED = -3,   /* max_iter reached; outputs hold the last iterate's values */
+    HMG_DIVERGED = -4,        /* a residual became NaN or Inf */
+    HMG_CUDA_ERROR = -5,      /* a CUDA runtime call failed; see hmg_last_error() */
+    HMG_BUSY = -6,            /* hmg_submit: queue full */
+    HMG_UNKNOWN_TICKET = -7   /* hmg_poll: no such request (or already collected) */
+} hmg_status;
+
+/* Arithmetic of the solve.
+ * HMG_FP64: every step in FP64 (the plain method of §3).
+ * HMG_FP32_BULK: FFTs and pointwise updates in FP32; residual norms, the convergence
+ *   tests, the flux average and a few defect-correction sweeps in FP64, so that the
+ *   same tolerance as HMG_FP64 is met (eps_eq < tol computed in FP64). */
+typedef enum { HMG_FP64 = 0, HMG_FP32_BULK = 1 } hmg_precision;
+
+/* Per-solve report.  Index j is the macroscopic gradient e_j. */
+typedef struct {
+    int iters[3];          /* sweeps of steps 2-7 (FP32 and FP64 together) */
+    int iters_fp64[3];     /* of which in FP64 */
+    double eps_comp[3];    /* last compatibility residual (§3 step 6) */
+    double eps_eq[3];      /* last equilibrium residual (§3 step 1) */
+    double seconds;        /* wall time of the call */
+    int fp64_rounds;       /* FP64 defect-correction rounds (HMG_FP32_BULK) */
+    int status[3];         /* hmg_status per gradient */
+} hmg_info;
+
+/* Library version string (static storage). */
+const char* hmg_version(void);
+
+/* Thread-local description of the last failure in this thread ("" if none). */
+const char* hmg_last_error(void);
+
+/* Create a context on CUDA device `device`.  `hbm_budget_bytes` caps the device
+ * memory the context may hold for solve state (0 = 90 % of the free memory at
+ * creation).  *ctx receives the handle; destroy it with hmg_destroy. */
+hmg_status hmg_create(hmg_ctx** ctx, int device, size_t hbm_budget_bytes);
+
+/* Release every resource of the context (waits for in-flight work). */
+hmg_status hmg_destroy(hmg_ctx* ctx);
+
+/* Voxelize coated spheres into a three-phase grid (§2, Fig. 1).
+ * spheres: n entries (host or device).  layer: l in (0, 1), core radius (1-l) r_s.
+ * phase_out: N^3 bytes (host or device), written with 0/1/2.
+ * Rule (bit-exact, integer): coordinates are quantized to S = 2 N 4096 units; voxel
+ * (i,j,k) has centre ((2i+1) 4096, ...); a centre c maps to floor(c' S + 1/2) mod S
+ * with c' = c - floor(c); squared radii are floor((r S)^2 + 1/2) and
+ * floor(((1-l) r S)^2 + 1/2); distances are periodic minimum-image; a voxel is
+ * inclusion if inside any core, else coating if inside any sphere, else matrix
+ * (boundaries inclusive).
+ * Errors: HMG_INVALID_ARG for n = 0 or n > 100000, non-finite values, r <= 0 or
+ * r >= 0.5, layer outside (0,1), a bad N, or overlapping spheres (§2: the spheres
+ * do not overlap). */
+hmg_status hmg_voxelize(hmg_ctx* ctx, const hmg_sphere* spheres, size_t n, double layer,
+                        int N, uint8_t* phase_out);
+
+/* Effective conductivity tensor of a three-phase grid (§3 Algorithm, steps 1-7, run
+ * for the three unit gradients; §3 last paragraph for L_hom).
+ * phase: N^3 bytes (host or device).  k_*: phase conductivities (> 0).
+ * tol: the convergence criterion acc of §3, used for both eps_comp and eps_eq.
+ * max_iter: cap on sweeps per gradient (<= 0 selects 20000).
+ * K_out: 9 doubles (host), row-major, K_out[3*i + j] = <k e_i> for gradient e_j,
+ *   i.e. L_hom with <phi> = -L_hom grad Theta (not symmetrized).
+ * info: optional (may be NULL).
+ * Returns HMG_OK when all three gradients converged, else the first failure. */
+hmg_status hmg_solve(hmg_ctx* ctx, const uint8_t* phase, int N, double k_matrix,
+                     double k_incl, double k_coat, double tol, hmg_precision precision,
+                     int max_iter, double K_out[9], hmg_info* info);
+
+/* hmg_solve that also returns the converged gradient fields.
+ * e_out: NULL or 9 N^3 doubles (host or device): gradient j's field, components
+ * x, y, z, at offset 3 j N^3.  Other arguments as hmg_solve. */
+hmg_status hmg_solve_fields(hmg_ctx* ctx, const uint8_t* phase, int N, double k_matrix,
+                            double k_incl, double k_coat, double tol,
+                            hmg_precision precision, int max_iter, double K_out[9],
+                            hmg_info* info, double* e_out);
+
+/* Run `n_iter` sweeps of steps 2-7 of §3 (no convergence test) on a given gradient
+ * field, for one macroscopic gradient grad_Theta (3 doubles, host).
+ * e_inout: 3 N^3 doubles (host or device), the current iterate e^n on entry and
+ * e^{n + n_iter} on return.  eps_comp_out: NULL or n_iter doubles (host), the
+ * step-6 residual of each sweep.  precision selects FP64 or FP32 arithmetic for
+ * the sweeps (the field is rounded to FP32 on entry in that case). */
+hmg_status hmg_em_iterate(hmg_ctx* ctx, const uint8_t* phase, int N, double k_matrix,
+                          double k_incl, double k_coat, const double grad_Theta[3],
+                          hmg_precision precision, int n_iter, double* e_inout,
+                          double* eps_comp_out);
+
+/* Equilibrium residual of step 1 of §3 for a gradient field e (3 N^3 doubles, host
+ * or device): phi = -k e, phi_hat = DFT(phi)/N^3,
+ * eps_eq = sqrt(sum_{xi != 0} |xi . phi_hat|^2) / |phi_hat(0)|.
+ * eps_eq_out: 1 double (host).  flux_mean_out: NULL or 3 doubles (host), <k e>
+ * (minus the mean flux of §3).  Arithmetic in FP64 or FP32 (accumulation in FP64). */
+hmg_status hmg_equilibrium(hmg_ctx* ctx, const uint8_t* phase, int N, double k_matrix,
+                           double k_incl, double k_coat, hmg_precision precision,
+                           const double* e, double* eps_eq_out, double* flux_mean_out);
+
+/* Unnormalized forward 3D DFT (§3 step 3) of `count` real N^3 grids.
+ * x: count N^3 doubles (host or device).
+ * X_out: count * N^3 complex values as interleaved (re, im) doubles (host or
+ * device), N*N*(N/2) complex per grid, index (kz*N + ky)*(N/2) + kx, kx in [0, N/2).
+ * For kx > 0 the entry is the DFT coefficient X(kx, ky, kz).  The kx = 0 entry packs
+ * two planes: Z = A + i B with A(ky,kz) = X(0, ky, kz) and B(ky,kz) = X(N/2, ky, kz);
+ * A = (Z(k) + conj Z(-k))/2 and B = (Z(k) - conj Z(-k))/(2i) recover them. */
+hmg_status hmg_fft_forward(hmg_ctx* ctx, int N, int count, hmg_precision precision,
+                           const double* x, double* X_out);
+
+/* Unnormalized inverse of hmg_fft_forward (kernel exp(+2 pi i k.n/N), no 1/N^3):
+ * X: packed spectra as produced by hmg_fft_forward; x_out: count N^3 doubles. */
+hmg_status hmg_fft_inverse(hmg_ctx* ctx, int N, int count, hmg_precision precision,
+                           const double* X, double* x_out);
+
+/* ---- many RVEs: batched solves and the request loop ------------------------- */
+
+/* Solve `count` RVEs (possibly of different N) together: each batched sweep
+ * advances every unfinished RVE and gradient in one launch per FFT pass.
+ * phases[i]: N_list[i]^3 bytes (host or device).  k3: 3 count doubles
+ * (k_matrix, k_incl, k_coat per RVE).  K_out: 9 count doubles (host).
+ * info: NULL or count entries.  Other arguments as hmg_solve. */
+hmg_status hmg_solve_batch(hmg_ctx* ctx, int count, const uint8_t* const* phases,
+                           const int* N_list, const double* k3, double tol,
+                           hmg_precision precision, int max_iter, double* K_out,
+                           hmg_info* info);
+
+/* Queue one solve request (copies the phase grid; returns without waiting for the
+ * GPU).  Requests run concurrently as device memory and slots allow (admission by
+ * HBM footprint against the context's budget).  *ticket identifies the request.
+ * Returns HMG_BUSY when the queue is full, HMG_INVALID_ARG for bad arguments, and
+ * HMG_OUT_OF_MEMORY when the request alone exceeds the budget. */
+hmg_status hmg_submit(hmg_ctx* ctx, const uint8_t* phase, int N, double k_matrix,
+                      double k_incl, double k_coat, double tol, hmg_precision precision,
+                      uint64_t* ticket);
+
+/* Result of a submitted request: HMG_PENDING while queued or running; otherwise the
+ * request's final status with K_out (9 doubles, host) and info (nullable) filled in.
+ * A finished ticket is released by the call that returns its result. */
+hmg_status hmg_poll(hmg_ctx* ctx, uint64_t ticket, double K_out[9], hmg_info* info);
+
+/* ---- tracing ------------------------------------------------------------------ */
+
+/* Kernel kinds reported by the tracer. */
+typedef enum {
+    HMG_K_X_FORWARD = 0,   /* x pass, real -> complex, polarization fused (step 2 + 3) */
+    HMG_K_Y_FORWARD = 1,   /* y pass forward (step 3) */
+    HMG_K_Z_GREEN = 2,     /* z forward + Green operator + z inverse (steps 3-5) */
+    HMG_K_Y_INVERSE = 3,   /* y pass inverse (step 5) */
+    HMG_K_X_INVERSE = 4,   /* x pass, complex -> real, update and residual (steps 5-7) */
+    HMG_K_EQ_X = 5,        /* equilibrium check: x pass with the flux average (step 1) */
+    HMG_K_EQ_Z = 6,        /* equilibrium check: z pass with the divergence norm (step 1) */
+    HMG_K_OTHER = 7,       /* reductions, conversions, voxelization */
+    HMG_K_COUNT = 8
+} hmg_kernel_kind;
+
+/* Start (enable = 1, counters reset) or stop (0) timing every kernel the solver
+ * launches with CUDA events recorded on the context's stream around each launch. */
+hmg_status hmg_trace_enable(hmg_ctx* ctx, int enable);
+
+/* Accumulated trace of one kernel kind: total device time (ms), launches, and the
+ * algorithmic bytes those launches had to move (fields read and written once each). */
+hmg_status hmg_trace_read(hmg_ctx* ctx, int kind, double* total_ms, long long* launches,
+                          double* algo_bytes);
+
+/* Device memory the solver state of one N^3 request occupies (bytes). */
+size_t hmg_footprint(int N, hmg_precision precision);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HMG_H */

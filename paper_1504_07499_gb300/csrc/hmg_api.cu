@@ -1,0 +1,575 @@
+// libhmg host runtime: contexts, FFT schedules, device buffers, the solve driver of
+// §3's Algorithm (FP64 and FP32-bulk with FP64 defect correction), and the C ABI.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/hmg.h"
+#include "hmg_internal.h"
+#include "hmg_runtime.h"
+
+namespace hmg {
+
+thread_local std::string g_last_error;
+
+void set_error(const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+}
+
+// ---------------------------------------------------------------------------
+// FFT schedules and twiddles
+// ---------------------------------------------------------------------------
+
+bool valid_length(int L) {
+    if (L < 1) return false;
+    while (L % 2 == 0) L /= 2;
+    while (L % 3 == 0) L /= 3;
+    return L == 1;
+}
+
+bool valid_N(int N) { return N >= 8 && N <= 512 && N % 2 == 0 && valid_length(N); }
+
+void make_plan(int L, FftPlan* p) {
+    int a = 0, b = 0, t = L;
+    while (t % 2 == 0) { t /= 2; ++a; }
+    while (t % 3 == 0) { t /= 3; ++b; }
+    p->L = L;
+    p->nst = 0;
+    for (int i = 0; i < b; ++i) p->rad[p->nst++] = 3;
+    int n8 = a / 3, rem = a % 3;
+    if (rem == 1 && n8 > 0) { --n8; rem = 4; }  // 16 = 4 * 4 instead of 8 * 2
+    for (int i = 0; i < n8; ++i) p->rad[p->nst++] = 8;
+    if (rem == 4) { p->rad[p->nst++] = 4; p->rad[p->nst++] = 4; }
+    else if (rem == 2) p->rad[p->nst++] = 4;
+    else if (rem == 1) p->rad[p->nst++] = 2;
+}
+
+static int pow2_divisor(long long v) {
+    int p = 1;
+    while (v % (2LL * p) == 0 && p < (1 << 20)) p *= 2;
+    return p;
+}
+
+GridPlan::~GridPlan() {
+    if (tw32) cudaFree(tw32);
+    if (tw64) cudaFree(tw64);
+}
+
+}  // namespace hmg
+
+std::shared_ptr<hmg::GridPlan> hmg_ctx::plan(int N) {
+    using namespace hmg;
+    auto it = plans.find(N);
+    if (it != plans.end()) return it->second;
+    auto gp = std::make_shared<GridPlan>();
+    gp->N = N;
+    const int M = N / 2;
+    make_plan(N, &gp->pN);
+    make_plan(M, &gp->pM);
+    gp->pN.tw_off = 0;
+    gp->pM.tw_off = N;
+    std::vector<double2> h64(N + M);
+    std::vector<float2> h32(N + M);
+    for (int part = 0; part < 2; ++part) {
+        const int L = part == 0 ? N : M;
+        const int off = part == 0 ? 0 : N;
+        for (int k = 0; k < L; ++k) {
+            // exp(-2 pi i k / L), evaluated with the octant symmetry so that
+            // w^(L/4) = -i, w^(L/2) = -1 hold exactly
+            const double ang = 2.0 * M_PI * (double)k / (double)L;
+            double c = std::cos(ang), s = -std::sin(ang);
+            if ((4 * k) % L == 0) {
+                const int qd = (4 * k) / L;
+                c = (qd == 0) ? 1.0 : (qd == 2 ? -1.0 : 0.0);
+                s = (qd == 1) ? -1.0 : (qd == 3 ? 1.0 : 0.0);
+            }
+            h64[off + k] = make_double2(c, s);
+            h32[off + k] = make_float2((float)c, (float)s);
+        }
+    }
+    if (cudaMalloc(&gp->tw64, sizeof(double2) * (N + M)) != cudaSuccess ||
+        cudaMalloc(&gp->tw32, sizeof(float2) * (N + M)) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    cudaMemcpy(gp->tw64, h64.data(), sizeof(double2) * (N + M), cudaMemcpyHostToDevice);
+    cudaMemcpy(gp->tw32, h32.data(), sizeof(float2) * (N + M), cudaMemcpyHostToDevice);
+    plans[N] = gp;
+    return gp;
+}
+
+namespace hmg {
+
+GridDesc make_desc(const GridPlan& gp, bool fp64, const double k[3], const uint8_t* phase_d,
+                   int nslots) {
+    GridDesc g;
+    memset(&g, 0, sizeof(g));
+    const int N = gp.N, M = N / 2;
+    g.N = N;
+    g.M = M;
+    g.NN = (long long)N * N;
+    g.N3 = g.NN * N;
+    g.NNM = g.NN * M;
+    g.pN = gp.pN;
+    g.pM = gp.pM;
+    g.tw32 = gp.tw32;
+    g.tw64 = gp.tw64;
+    const double kmin = std::min(k[0], std::min(k[1], k[2]));
+    const double kmax = std::max(k[0], std::max(k[1], k[2]));
+    const double k0 = std::sqrt(kmin * kmax);
+    g.k0 = k0;
+    for (int p = 0; p < 3; ++p) {
+        g.Y[p] = (k[p] - k0) / (k[p] + k0);
+        g.W[p] = k[p] / (k[p] + k0);
+        g.KP[p] = k[p] + k0;
+    }
+    for (int s = 0; s < kMaxSlots; ++s)
+        for (int c = 0; c < 3; ++c) g.E[s][c] = (s == c) ? 1.0 : 0.0;
+    g.nslots = nslots;
+    const int tile = fp64 ? 1024 : 2048;        // complex values per x-pass CTA buffer
+    int rows = 1;
+    while (rows * 2 * M <= tile) rows *= 2;
+    rows = std::min(rows, pow2_divisor(g.NN));
+    g.rows = rows;
+    const int pm = pow2_divisor(M);
+    g.Py = std::min(fp64 ? 8 : 16, pm);
+    g.Pz = std::min(fp64 ? 4 : 8, pm);
+    g.phase = phase_d;
+    return g;
+}
+
+// ---------------------------------------------------------------------------
+// device buffers
+// ---------------------------------------------------------------------------
+
+}  // namespace hmg
+
+void* hmg_ctx::alloc(size_t bytes) {
+    if (bytes == 0) return nullptr;
+    if (budget && used + bytes > budget) return nullptr;
+    void* p = nullptr;
+    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    used += bytes;
+    sizes[p] = bytes;
+    return p;
+}
+
+void hmg_ctx::release(void* p) {
+    if (!p) return;
+    auto it = sizes.find(p);
+    if (it != sizes.end()) {
+        used -= it->second;
+        sizes.erase(it);
+    }
+    cudaFree(p);
+}
+
+namespace hmg {
+
+size_t state_bytes(int N, bool fp64, int nslots) {
+    const size_t N3 = (size_t)N * N * N;
+    const size_t field64 = (size_t)nslots * 3 * N3 * 8;
+    const size_t field32 = (size_t)nslots * 3 * N3 * 4;
+    size_t b = N3 + 2 * field64;                        // phase, tau64, spec64
+    if (!fp64) b += 3 * field32;                        // f32, r32, spec32
+    b += (size_t)nslots * 2 * 4 * (3 * (size_t)N * N) * 8 + 4096;   // partials
+    return b;
+}
+
+bool SolveState::ensure(Context* c, int N_, bool fp64_, int nslots_) {
+    // a bulk (FP32 + FP64) state also serves FP64 requests
+    if (N == N_ && (fp64 == fp64_ || (fp64_ && !fp64)) && nslots >= nslots_) return true;
+    free_all(c);
+    N = N_;
+    fp64 = fp64_;
+    nslots = nslots_;
+    const size_t N3 = (size_t)N * N * N;
+    const size_t f64 = (size_t)nslots * 3 * N3 * 8, f32 = (size_t)nslots * 3 * N3 * 4;
+    phase = (uint8_t*)c->alloc(N3);
+    tau64 = (double*)c->alloc(f64);
+    spec64 = c->alloc(f64);
+    if (!fp64) {
+        f32buf = (float*)c->alloc(f32);
+        r32 = (float*)c->alloc(f32);
+        spec32 = c->alloc(f32);
+    }
+    const size_t np = (size_t)nslots * 4 * 3 * N * N + 64;
+    partial = (double*)c->alloc(np * sizeof(double));
+    partial2 = (double*)c->alloc(np * sizeof(double));
+    red = (double*)c->alloc(64 * sizeof(double));
+    bool ok = phase && tau64 && spec64 && partial && partial2 && red && (fp64 || (f32buf && r32 && spec32));
+    if (!ok) {
+        free_all(c);
+        return false;
+    }
+    return true;
+}
+
+void SolveState::free_all(Context* c) {
+    for (void** p : {(void**)&phase, (void**)&tau64, &spec64, (void**)&f32buf, (void**)&r32, &spec32,
+                     (void**)&partial, (void**)&partial2, (void**)&red}) {
+        c->release(*p);
+        *p = nullptr;
+    }
+    N = 0;
+}
+
+// ---------------------------------------------------------------------------
+// pointer helpers
+// ---------------------------------------------------------------------------
+
+bool is_device_ptr(const void* p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+cudaError_t copy_in(void* dst_dev, const void* src, size_t bytes, cudaStream_t st) {
+    return cudaMemcpyAsync(dst_dev, src, bytes, is_device_ptr(src) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st);
+}
+
+cudaError_t copy_out(void* dst, const void* src_dev, size_t bytes, cudaStream_t st) {
+    return cudaMemcpyAsync(dst, src_dev, bytes, is_device_ptr(dst) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st);
+}
+
+// ---------------------------------------------------------------------------
+// one sweep of steps 2-7 and the step-1 equilibrium check
+// ---------------------------------------------------------------------------
+
+int Tracer::begin(cudaStream_t st) {
+    if (!on) return -1;
+    int idx;
+    if (!free_pairs.empty()) {
+        idx = free_pairs.back();
+        free_pairs.pop_back();
+    } else {
+        cudaEvent_t a, b;
+        if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) {
+            cudaGetLastError();
+            return -1;
+        }
+        idx = (int)events.size() / 2;
+        events.push_back(a);
+        events.push_back(b);
+    }
+    cudaEventRecord(events[2 * idx], st);
+    return idx;
+}
+
+void Tracer::end(int ev, int kind, double b, cudaStream_t st) {
+    if (ev < 0) return;
+    cudaEventRecord(events[2 * ev + 1], st);
+    pending.push_back({kind, ev, b});
+}
+
+void Tracer::collect() {
+    for (const Pending& p : pending) {
+        float t = 0.f;
+        if (cudaEventElapsedTime(&t, events[2 * p.ev], events[2 * p.ev + 1]) == cudaSuccess) {
+            ms[p.kind] += t;
+            launches[p.kind] += 1;
+            bytes[p.kind] += p.bytes;
+        } else {
+            cudaGetLastError();
+        }
+        free_pairs.push_back(p.ev);
+    }
+    pending.clear();
+}
+
+void Tracer::reset() {
+    collect();
+    for (int k = 0; k < HMG_K_COUNT; ++k) {
+        ms[k] = 0;
+        launches[k] = 0;
+        bytes[k] = 0;
+    }
+}
+
+Tracer::~Tracer() {
+    for (cudaEvent_t e : events) cudaEventDestroy(e);
+}
+
+static int popc(unsigned m) { return __builtin_popcount(m); }
+
+// Each launch is bracketed by tracer events when tracing is on.
+#define HMG_TRACED(KIND, BYTES, CALL)          \
+    do {                                       \
+        int ev_ = tr ? tr->begin(st) : -1;     \
+        CALL;                                  \
+        if (tr) tr->end(ev_, KIND, BYTES, st); \
+    } while (0)
+
+template <typename R>
+void Solver::sweep(unsigned mask, R* field, void* spec, int zmode, int ximode, const float* r32in,
+                   float* d32, float* r32out) {
+    const double f = (double)popc(mask) * 3.0 * (double)g.N3;   // field elements moved per array
+    const double F = sizeof(R);
+    HMG_TRACED(HMG_K_X_FORWARD, f * 2 * F + (double)g.N3,
+               launch_x_forward<R>(g, XF_POLARIZE, mask, field, spec, nullptr, st));
+    HMG_TRACED(HMG_K_Y_FORWARD, f * 2 * F, launch_y_pass<R>(g, true, mask, spec, st));
+    HMG_TRACED(HMG_K_Z_GREEN, f * 2 * F, launch_z_pass<R>(g, zmode, mask, spec, nullptr, st));
+    HMG_TRACED(HMG_K_Y_INVERSE, f * 2 * F, launch_y_pass<R>(g, false, mask, spec, st));
+    double xb = f * 2 * F;                                       // spectrum in, field out
+    if (ximode == XI_INPLACE_RES) xb += f * F;                  // old field for the residual
+    if (ximode == XI_ADD_R_RES) xb += f * F + f * 4;            // old field and r
+    if (ximode == XI_DIFF) xb = f * F + f * F + 2 * f * 4;      // spectrum, old field, d and r out
+    HMG_TRACED(HMG_K_X_INVERSE, xb,
+               launch_x_inverse<R>(g, ximode, mask, spec, field, r32in, d32, r32out, s->partial, st));
+    HMG_TRACED(HMG_K_OTHER, 0.0, launch_reduce(s->partial, g.nslots, x_ctas(g), 1, s->red, st));
+}
+
+template <typename R>
+void Solver::equilibrium(unsigned mask, const R* field, void* spec) {
+    const double f = (double)popc(mask) * 3.0 * (double)g.N3;
+    const double F = sizeof(R);
+    HMG_TRACED(HMG_K_EQ_X, f * 2 * F + (double)g.N3,
+               launch_x_forward<R>(g, XF_FLUX, mask, field, spec, s->partial, st));
+    HMG_TRACED(HMG_K_OTHER, 0.0, launch_reduce(s->partial, g.nslots, x_ctas(g), 3, s->red + 16, st));
+    HMG_TRACED(HMG_K_Y_FORWARD, f * 2 * F, launch_y_pass<R>(g, true, mask, spec, st));
+    HMG_TRACED(HMG_K_EQ_Z, f * F, launch_z_pass<R>(g, Z_EQ, mask, spec, s->partial2, st));
+    HMG_TRACED(HMG_K_OTHER, 0.0, launch_reduce(s->partial2, g.nslots, z_ctas(g), 1, s->red + 32, st));
+}
+
+bool Solver::fetch(double* h, int off, int count) {
+    cudaError_t e = cudaMemcpyAsync(h, s->red + off, count * sizeof(double), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        set_error("CUDA error: %s", cudaGetErrorString(e));
+        return false;
+    }
+    if (tr) tr->collect();
+    return true;
+}
+
+// eps_comp from the sum of squared tau differences: |e^n - e_comp^n| = |dtau| / (2 k0)
+double Solver::eps_from_sum(double sum, int slot) const {
+    const double nE = std::sqrt(g.E[slot][0] * g.E[slot][0] + g.E[slot][1] * g.E[slot][1] +
+                                g.E[slot][2] * g.E[slot][2]);
+    return std::sqrt(sum / (double)g.N3) / (2.0 * g.k0 * nE);
+}
+
+// eq check of the slots in `mask`; fills eps_eq and the mean flux <k e>
+template <typename R>
+bool Solver::check_eq(unsigned mask, const R* field, void* spec, double eps_eq[3], double flux[3][3]) {
+    equilibrium<R>(mask, field, spec);
+    double h[48];
+    if (!fetch(h, 16, 32)) return false;
+    for (int sl = 0; sl < g.nslots; ++sl) {
+        if (!((mask >> sl) & 1u)) continue;
+        double nrm = 0.0;
+        for (int c = 0; c < 3; ++c) {
+            flux[sl][c] = h[sl * 3 + c] / (double)g.N3;
+            nrm += flux[sl][c] * flux[sl][c];
+        }
+        eps_eq[sl] = std::sqrt(h[16 + sl]) / std::sqrt(nrm);
+    }
+    return true;
+}
+
+// Plain FP64 method: the Algorithm of §3 in its printed order.
+hmg_status Solver::run_fp64(int max_iter, double tol, hmg_info* info, double K[9]) {
+    const unsigned all = (1u << g.nslots) - 1u;
+    launch_init_tau<double>(g, all, s->tau64, st);
+    double eps_comp[3] = {INFINITY, INFINITY, INFINITY}, eps_eq[3] = {INFINITY, INFINITY, INFINITY};
+    double flux[3][3] = {};
+    int iters[3] = {0, 0, 0}, status[3] = {HMG_NOT_CONVERGED, HMG_NOT_CONVERGED, HMG_NOT_CONVERGED};
+    unsigned active = all;
+    for (int n = 0; n < max_iter && active; ++n) {
+        unsigned eqm = 0;
+        for (int sl = 0; sl < g.nslots; ++sl)
+            if (((active >> sl) & 1u) && eps_comp[sl] < tol) eqm |= 1u << sl;
+        if (eqm) {  // step 1
+            if (!check_eq<double>(eqm, s->tau64, s->spec64, eps_eq, flux)) return HMG_CUDA_ERROR;
+            for (int sl = 0; sl < g.nslots; ++sl)
+                if (((eqm >> sl) & 1u) && eps_eq[sl] < tol) {
+                    status[sl] = HMG_OK;
+                    active &= ~(1u << sl);
+                }
+            if (!active) break;
+        }
+        sweep<double>(active, s->tau64, s->spec64, Z_ITER, XI_INPLACE_RES, nullptr, nullptr, nullptr);
+        double h[3];
+        if (!fetch(h, 0, g.nslots)) return HMG_CUDA_ERROR;
+        for (int sl = 0; sl < g.nslots; ++sl) {
+            if (!((active >> sl) & 1u)) continue;
+            ++iters[sl];
+            eps_comp[sl] = eps_from_sum(h[sl], sl);
+            if (!std::isfinite(eps_comp[sl])) {
+                status[sl] = HMG_DIVERGED;
+                active &= ~(1u << sl);
+            }
+        }
+    }
+    // slots that ran out of sweeps: report the last iterate
+    unsigned left = 0;
+    for (int sl = 0; sl < g.nslots; ++sl)
+        if (status[sl] == HMG_NOT_CONVERGED) left |= 1u << sl;
+    if (left && !check_eq<double>(left, s->tau64, s->spec64, eps_eq, flux)) return HMG_CUDA_ERROR;
+    return finish(status, iters, iters, eps_comp, eps_eq, flux, 0, info, K);
+}
+
+// FP32 bulk: FP32 sweeps until the FP32 residual stalls, then FP64 defect correction
+// rounds: r = T tau64 + b - tau64 (one FP64 sweep), FP32 sweeps on delta = T delta + r,
+// tau64 += delta, until the FP64 residuals meet the tolerance.
+hmg_status Solver::run_bulk(int max_iter, double tol, hmg_info* info, double K[9]) {
+    enum { PH_A = 0, PH_OUTER = 1, PH_INNER = 2, PH_DONE = 3 };
+    const unsigned all = (1u << g.nslots) - 1u;
+    launch_init_tau<float>(g, all, s->f32buf, st);
+    int state[3], iters[3] = {0, 0, 0}, it64[3] = {0, 0, 0}, status[3];
+    double eps_comp[3] = {INFINITY, INFINITY, INFINITY}, eps_eq[3] = {INFINITY, INFINITY, INFINITY};
+    double eps32[3] = {INFINITY, INFINITY, INFINITY}, best[3], outer_eps[3] = {INFINITY, INFINITY, INFINITY};
+    int since_best[3] = {0, 0, 0}, inner_n[3] = {0, 0, 0};
+    double flux[3][3] = {};
+    int rounds = 0;
+    for (int sl = 0; sl < 3; ++sl) {
+        state[sl] = sl < g.nslots ? PH_A : PH_DONE;
+        status[sl] = HMG_NOT_CONVERGED;
+        best[sl] = INFINITY;
+    }
+    const double thetaA = std::max(tol, 1e-6);
+    const double eta = 1e-4;           // inner solves reduce the outer residual by this factor
+    const int stall = 25;              // sweeps without a new best residual = FP32 floor
+    auto mask_of = [&](int ph) {
+        unsigned m = 0;
+        for (int sl = 0; sl < g.nslots; ++sl)
+            if (state[sl] == ph) m |= 1u << sl;
+        return m;
+    };
+    int total = 0;
+    while (mask_of(PH_DONE) != all) {
+        if (total >= max_iter) break;
+        ++total;
+        // FP64 outer sweep
+        unsigned mo = mask_of(PH_OUTER);
+        if (mo) {
+            sweep<double>(mo, s->tau64, s->spec64, Z_ITER, XI_DIFF, nullptr, s->f32buf, s->r32);
+            double h[3];
+            if (!fetch(h, 0, g.nslots)) return HMG_CUDA_ERROR;
+            unsigned eqm = 0;
+            for (int sl = 0; sl < g.nslots; ++sl) {
+                if (!((mo >> sl) & 1u)) continue;
+                ++iters[sl];
+                ++it64[sl];
+                eps_comp[sl] = eps_from_sum(h[sl], sl);
+                outer_eps[sl] = eps_comp[sl];
+                if (!std::isfinite(eps_comp[sl])) {
+                    status[sl] = HMG_DIVERGED;
+                    state[sl] = PH_DONE;
+                } else if (eps_comp[sl] < tol) {
+                    eqm |= 1u << sl;
+                }
+            }
+            if (eqm) {
+                if (!check_eq<double>(eqm, s->tau64, s->spec64, eps_eq, flux)) return HMG_CUDA_ERROR;
+                for (int sl = 0; sl < g.nslots; ++sl)
+                    if (((eqm >> sl) & 1u) && eps_eq[sl] < tol) {
+                        status[sl] = HMG_OK;
+                        state[sl] = PH_DONE;
+                    }
+            }
+            for (int sl = 0; sl < g.nslots; ++sl)
+                if (((mo >> sl) & 1u) && state[sl] == PH_OUTER) {
+                    state[sl] = PH_INNER;
+                    best[sl] = INFINITY;
+                    since_best[sl] = 0;
+                    inner_n[sl] = 0;
+                    ++rounds;
+                }
+            continue;
+        }
+        // FP32 sweeps: plain (phase A) and defect-correction (inner)
+        unsigned ma = mask_of(PH_A), mi = mask_of(PH_INNER);
+        if (ma) sweep<float>(ma, s->f32buf, s->spec32, Z_ITER, XI_INPLACE_RES, nullptr, nullptr, nullptr);
+        double ha[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+        if (ma && !fetch(ha, 0, g.nslots)) return HMG_CUDA_ERROR;
+        if (mi) sweep<float>(mi, s->f32buf, s->spec32, Z_ITER_NOB, XI_ADD_R_RES, s->r32, nullptr, nullptr);
+        if (mi && !fetch(hi, 0, g.nslots)) return HMG_CUDA_ERROR;
+        unsigned to_outer_a = 0, to_outer_i = 0;
+        for (int sl = 0; sl < g.nslots; ++sl) {
+            const bool a = (ma >> sl) & 1u, in = (mi >> sl) & 1u;
+            if (!a && !in) continue;
+            ++iters[sl];
+            eps32[sl] = eps_from_sum(a ? ha[sl] : hi[sl], sl);
+            if (!std::isfinite(eps32[sl])) {
+                status[sl] = HMG_DIVERGED;
+                state[sl] = PH_DONE;
+                continue;
+            }
+            if (eps32[sl] < best[sl] * 0.999) {
+                best[sl] = eps32[sl];
+                since_best[sl] = 0;
+            } else {
+                ++since_best[sl];
+            }
+            if (a) {
+                eps_comp[sl] = eps32[sl];
+                if (eps32[sl] < thetaA || since_best[sl] >= stall) to_outer_a |= 1u << sl;
+            } else {
+                ++inner_n[sl];
+                if (eps32[sl] < eta * outer_eps[sl] || since_best[sl] >= stall) to_outer_i |= 1u << sl;
+            }
+        }
+        if (to_outer_a) launch_widen(g, to_outer_a, s->f32buf, s->tau64, st);
+        if (to_outer_i) launch_axpy(g, to_outer_i, s->f32buf, s->tau64, st);
+        for (int sl = 0; sl < g.nslots; ++sl)
+            if (((to_outer_a | to_outer_i) >> sl) & 1u) state[sl] = PH_OUTER;
+    }
+    unsigned left = 0;
+    for (int sl = 0; sl < g.nslots; ++sl)
+        if (status[sl] == HMG_NOT_CONVERGED) {
+            if (state[sl] == PH_A) launch_widen(g, 1u << sl, s->f32buf, s->tau64, st);
+            if (state[sl] == PH_INNER) launch_axpy(g, 1u << sl, s->f32buf, s->tau64, st);
+            left |= 1u << sl;
+        }
+    if (left && !check_eq<double>(left, s->tau64, s->spec64, eps_eq, flux)) return HMG_CUDA_ERROR;
+    return finish(status, iters, it64, eps_comp, eps_eq, flux, rounds, info, K);
+}
+
+hmg_status Solver::finish(const int status[3], const int iters[3], const int it64[3], const double eps_comp[3],
+                          const double eps_eq[3], const double flux[3][3], int rounds, hmg_info* info,
+                          double K[9]) {
+    for (int j = 0; j < 3; ++j)
+        for (int i = 0; i < 3; ++i) K[3 * i + j] = j < g.nslots ? flux[j][i] : 0.0;
+    if (info) {
+        for (int j = 0; j < 3; ++j) {
+            info->iters[j] = iters[j];
+            info->iters_fp64[j] = it64[j];
+            info->eps_comp[j] = eps_comp[j];
+            info->eps_eq[j] = eps_eq[j];
+            info->status[j] = status[j];
+        }
+        info->fp64_rounds = rounds;
+    }
+    for (int j = 0; j < g.nslots; ++j)
+        if (status[j] != HMG_OK) return (hmg_status)status[j];
+    return HMG_OK;
+}
+
+template void Solver::sweep<float>(unsigned, float*, void*, int, int, const float*, float*, float*);
+template void Solver::sweep<double>(unsigned, double*, void*, int, int, const float*, float*, float*);
+template bool Solver::check_eq<float>(unsigned, const float*, void*, double*, double (*)[3]);
+template bool Solver::check_eq<double>(unsigned, const double*, void*, double*, double (*)[3]);
+
+}  // namespace hmg

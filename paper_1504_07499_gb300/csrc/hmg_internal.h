@@ -1,0 +1,90 @@
+// Internal declarations shared by the libhmg translation units (host + device).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+namespace hmg {
+
+constexpr int kThreads = 256;      // threads per CTA in every FFT pass
+constexpr int kMaxStages = 12;     // radix stages per 1D transform
+constexpr int kMaxSlots = 3;       // right-hand sides (unit gradients) per RVE
+
+// Mixed-radix Stockham schedule of one 1D length (radices 2, 3, 4, 8).
+struct FftPlan {
+    int L;                 // transform length
+    int nst;               // number of stages
+    int rad[kMaxStages];   // radix of each stage, first stage first
+    int tw_off;            // offset of the length-L twiddle table exp(-2 pi i k / L)
+};
+
+// Everything a pass kernel needs about one RVE: sizes, FFT schedules, the
+// per-phase coefficient table, and the device fields (FP32 or FP64 copies).
+struct GridDesc {
+    int N, M;              // grid size and N/2 (complex length of an x row)
+    long long NN, N3;      // N*N and N^3
+    long long NNM;         // complex entries per component spectrum: N*N*M
+    FftPlan pN, pM;        // schedules for lengths N (y, z) and M (x)
+    const float2* tw32;    // twiddle tables (all lengths, concatenated)
+    const double2* tw64;
+    // per-phase coefficients, k0 = sqrt(min k * max k):
+    double Y[3];           // (k - k0)/(k + k0): polarization factor of the sweep
+    double W[3];           // k/(k + k0): flux factor, phi = W tau
+    double KP[3];          // k + k0: tau = (k + k0) e
+    double k0;
+    double E[kMaxSlots][3];  // macroscopic gradient of each right-hand side
+    int nslots;            // right-hand sides held in the fields
+    int rows;              // x-pass rows per CTA
+    int Py, Pz;            // columns per CTA in the y and z passes
+    const uint8_t* phase;  // N^3 phase ids
+};
+
+enum XFwdMode { XF_PLAIN = 0, XF_POLARIZE = 1, XF_FLUX = 2 };
+enum XInvMode { XI_PLAIN = 0, XI_INPLACE = 1, XI_INPLACE_RES = 2, XI_ADD_R_RES = 3, XI_DIFF = 4 };
+enum ZMode { Z_FWD = 0, Z_INV = 1, Z_ITER = 2, Z_ITER_NOB = 3, Z_EQ = 4 };
+
+// Launch wrappers (hmg_kernels.cu).  `mask` selects the active right-hand sides;
+// CTAs of inactive ones exit at once.  Partial-sum buffers receive one double per
+// CTA and right-hand side (layout [slot][cta]).
+template <typename R>
+void launch_x_forward(const GridDesc& g, int mode, unsigned mask, const R* tau,
+                      void* spec, double* partial, cudaStream_t st);
+template <typename R>
+void launch_y_pass(const GridDesc& g, bool forward, unsigned mask, void* spec, cudaStream_t st);
+template <typename R>
+void launch_z_pass(const GridDesc& g, int mode, unsigned mask, void* spec, double* partial,
+                   cudaStream_t st);
+// x inverse: writes tau (INPLACE*), adds r (ADD_R_RES), or writes d = new - old to
+// d32 and r32 without touching tau (DIFF).  Residual modes add (new-old)^2 per CTA.
+template <typename R>
+void launch_x_inverse(const GridDesc& g, int mode, unsigned mask, const void* spec, R* tau,
+                      const float* r32, float* d32, float* r32_out, double* partial,
+                      cudaStream_t st);
+
+int x_ctas(const GridDesc& g);   // CTAs per right-hand side of the x passes
+int z_ctas(const GridDesc& g);   // CTAs per right-hand side of the z pass
+
+// Sum `count` partials of each of `nslots` rows in a fixed order: out[s] = sum_i p[s*count+i].
+// `groups` > 1 splits each row into that many equal consecutive groups (out[s*groups+g]).
+void launch_reduce(const double* partial, int nslots, int count, int groups, double* out,
+                   cudaStream_t st);
+
+// Pointwise helpers on the fields.
+template <typename R>
+void launch_init_tau(const GridDesc& g, unsigned mask, R* tau, cudaStream_t st);
+template <typename R>
+void launch_e_to_tau(const GridDesc& g, int slot, const double* e, R* tau, cudaStream_t st);
+template <typename R>
+void launch_tau_to_e(const GridDesc& g, int slot, const R* tau, double* e, cudaStream_t st);
+void launch_widen(const GridDesc& g, unsigned mask, const float* src, double* dst, cudaStream_t st);
+void launch_axpy(const GridDesc& g, unsigned mask, const float* d, double* tau, cudaStream_t st);
+template <typename R>
+void launch_convert(const double* src, R* dst, long long n, cudaStream_t st);
+template <typename R>
+void launch_convert_back(const R* src, double* dst, long long n, cudaStream_t st);
+
+// Voxelization (hmg_voxelize.cu): q holds n quantized spheres (cx, cy, cz, R_out^2, R_in^2).
+void launch_voxelize(const long long* q, int n, int N, long long S, uint8_t* out, cudaStream_t st);
+
+}  // namespace hmg

@@ -1,0 +1,586 @@
+// FFT passes of one Eyre-Milton sweep (§3 Algorithm, steps 2-7) and the helpers
+// around them.  The 3D real transform runs as five passes over HBM:
+//   x forward (real->complex, polarization of step 2 fused on load),
+//   y forward,
+//   z forward + Green operator of step 4 (+ macroscopic gradient at DC) + z inverse,
+//   y inverse,
+//   x inverse (complex->real) with the update of step 7 written out and the
+//   step-6 residual accumulated in FP64.
+// The sweep is written in the polarization variable tau = (k + k0) e: with
+// Y = (k - k0)/(k + k0) and P the projector xi xi^T/|xi|^2 (Gamma0 = -P/k0 for
+// L0 = -k0 I), steps 2-7 read tau^{n+1} = (I - 2P)(Y tau^n) + 2 k0 E, and
+// e^n - e_comp^n = (tau^n - tau^{n+1}) / (2 k0), so no field but tau is stored.
+//
+// Spectrum layout: after the x pass each row of N reals becomes N/2 complex values
+// (x-major rows, same byte size as the real field); entry kx = 0 packs the two real
+// planes kx = 0 and kx = N/2 as X(0) + i X(N/2).  The y and z passes transform that
+// packed column like any other; the Green operator treats its four special modes
+// (ky, kz in {0, N/2}) by real and imaginary part.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "hmg_fft.cuh"
+#include "hmg_internal.h"
+
+namespace hmg {
+
+// ---------------------------------------------------------------------------
+// small device helpers
+// ---------------------------------------------------------------------------
+
+template <typename R>
+__device__ __forceinline__ R sel3(int ph, double a, double b, double c) {
+    return R(ph == 0 ? a : (ph == 1 ? b : c));
+}
+
+// Fixed-order CTA sum of one double per thread; result valid in thread 0.
+__device__ double block_sum(double v, double* sh) {
+    sh[threadIdx.x] = v;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+        __syncthreads();
+    }
+    double r = sh[0];
+    __syncthreads();
+    return r;
+}
+
+__device__ __forceinline__ int signed_mode(int k, int N) { return k <= N / 2 ? k : k - N; }
+
+// ---------------------------------------------------------------------------
+// x forward: rows of N reals -> N/2 packed complex values
+// ---------------------------------------------------------------------------
+
+template <typename R, int MODE>
+__global__ void __launch_bounds__(kThreads)
+k_x_forward(GridDesc g, unsigned mask, const R* __restrict__ tau, typename Cplx<R>::T* __restrict__ spec,
+            double* __restrict__ partial) {
+    using T2 = typename Cplx<R>::T;
+    const int slot = blockIdx.y;
+    if (!((mask >> slot) & 1u)) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T2* b0 = reinterpret_cast<T2*>(smem_raw);
+    const int M = g.M, N = g.N, rows = g.rows;
+    T2* b1 = b0 + rows * M;
+    __shared__ double red[kThreads];
+
+    const long long row0 = (long long)blockIdx.x * rows;   // row = c*NN + z*N + y
+    const T2* src = reinterpret_cast<const T2*>(tau + (long long)slot * 3 * g.N3 + row0 * N);
+    double acc = 0.0;
+    for (int q = threadIdx.x; q < rows * M; q += blockDim.x) {
+        const int rr = q / M, n = q - rr * M;
+        T2 v = src[(long long)rr * M + n];
+        if (MODE != XF_PLAIN) {
+            const long long prow = (row0 + rr) % g.NN;   // (z, y) row of the phase grid
+            const uchar2 ph = *reinterpret_cast<const uchar2*>(g.phase + prow * N + 2 * n);
+            R ca, cb;
+            if (MODE == XF_POLARIZE) {
+                ca = sel3<R>(ph.x, g.Y[0], g.Y[1], g.Y[2]);
+                cb = sel3<R>(ph.y, g.Y[0], g.Y[1], g.Y[2]);
+            } else {
+                ca = sel3<R>(ph.x, g.W[0], g.W[1], g.W[2]);
+                cb = sel3<R>(ph.y, g.W[0], g.W[1], g.W[2]);
+            }
+            v.x *= ca;
+            v.y *= cb;
+            if (MODE == XF_FLUX) acc += (double)v.x + (double)v.y;
+        }
+        b0[q] = v;
+    }
+    if (MODE == XF_FLUX) {
+        double s = block_sum(acc, red);
+        if (threadIdx.x == 0) partial[(long long)slot * gridDim.x + blockIdx.x] = s;
+    }
+    __syncthreads();
+    T2* res = fft_smem<true>(b0, b1, g.pM, TwTable<T2>::get(g), rows, M, 1);
+    // real-to-complex split: X_k = E_k + w_N^k O_k with E, O the DFTs of the even and
+    // odd samples, E_k = (Z_k + conj Z_{M-k})/2, O_k = (Z_k - conj Z_{M-k})/(2i)
+    const T2* twN = TwTable<T2>::get(g) + g.pN.tw_off;
+    T2* dst = spec + (long long)slot * 3 * g.NNM + row0 * M;
+    for (int q = threadIdx.x; q < rows * M; q += blockDim.x) {
+        const int rr = q / M, k = q - rr * M;
+        const T2 z = res[rr * M + k];
+        T2 out;
+        if (k == 0) {
+            out = mk(z.x + z.y, z.x - z.y);
+        } else {
+            const T2 zm = res[rr * M + (M - k)];
+            const T2 e = mk(R(0.5) * (z.x + zm.x), R(0.5) * (z.y - zm.y));
+            const T2 o = mk(R(0.5) * (z.y + zm.y), R(-0.5) * (z.x - zm.x));
+            out = cadd(e, cmul(o, __ldg(&twN[k])));
+        }
+        dst[(long long)rr * M + k] = out;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// x inverse: N/2 packed complex values -> N reals, with the sweep's output step
+// ---------------------------------------------------------------------------
+
+template <typename R, int MODE>
+__global__ void __launch_bounds__(kThreads)
+k_x_inverse(GridDesc g, unsigned mask, const typename Cplx<R>::T* __restrict__ spec, R* __restrict__ tau,
+            const float* __restrict__ r32, float* __restrict__ d32, float* __restrict__ r32_out,
+            double* __restrict__ partial) {
+    using T2 = typename Cplx<R>::T;
+    const int slot = blockIdx.y;
+    if (!((mask >> slot) & 1u)) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T2* b0 = reinterpret_cast<T2*>(smem_raw);
+    const int M = g.M, N = g.N, rows = g.rows;
+    T2* b1 = b0 + rows * M;
+    __shared__ double red[kThreads];
+
+    const long long row0 = (long long)blockIdx.x * rows;
+    const T2* src = spec + (long long)slot * 3 * g.NNM + row0 * M;
+    for (int q = threadIdx.x; q < rows * M; q += blockDim.x) b1[q] = src[q];
+    __syncthreads();
+    // complex-to-real merge: Z'_k = (X_k + conj X_{M-k}) + i w_N^{-k} (X_k - conj X_{M-k}),
+    // whose length-M inverse DFT gives N x[2n] + i N x[2n+1] (unnormalized)
+    const T2* twN = TwTable<T2>::get(g) + g.pN.tw_off;
+    for (int q = threadIdx.x; q < rows * M; q += blockDim.x) {
+        const int rr = q / M, k = q - rr * M;
+        T2 xk, xm;
+        if (k == 0) {
+            const T2 p = b1[rr * M];
+            xk = mk(p.x, R(0));
+            xm = mk(p.y, R(0));
+        } else {
+            xk = b1[rr * M + k];
+            xm = b1[rr * M + (M - k)];
+        }
+        const T2 s = mk(xk.x + xm.x, xk.y - xm.y);          // X_k + conj X_{M-k}
+        const T2 d = mk(xk.x - xm.x, xk.y + xm.y);          // X_k - conj X_{M-k}
+        const T2 dw = cmulc(d, __ldg(&twN[k]));             // d * w^{-k}
+        b0[q] = mk(s.x - dw.y, s.y + dw.x);                 // s + i dw
+    }
+    __syncthreads();
+    T2* res = fft_smem<false>(b0, b1, g.pM, TwTable<T2>::get(g), rows, M, 1);
+
+    const long long fbase = (long long)slot * 3 * g.N3 + row0 * N;   // element offset of the tile
+    T2* out = reinterpret_cast<T2*>(tau + fbase);
+    double acc = 0.0;
+    for (int q = threadIdx.x; q < rows * M; q += blockDim.x) {
+        T2 v = res[q];
+        if (MODE == XI_PLAIN || MODE == XI_INPLACE) {
+            out[q] = v;
+        } else if (MODE == XI_INPLACE_RES) {
+            const T2 o = out[q];
+            const double da = (double)v.x - (double)o.x, db = (double)v.y - (double)o.y;
+            acc += da * da + db * db;
+            out[q] = v;
+        } else if (MODE == XI_ADD_R_RES) {
+            const float2 rv = reinterpret_cast<const float2*>(r32 + fbase)[q];
+            v.x += R(rv.x);
+            v.y += R(rv.y);
+            const T2 o = out[q];
+            const double da = (double)v.x - (double)o.x, db = (double)v.y - (double)o.y;
+            acc += da * da + db * db;
+            out[q] = v;
+        } else {  // XI_DIFF: d = new - old, tau untouched
+            const T2 o = out[q];
+            const double da = (double)v.x - (double)o.x, db = (double)v.y - (double)o.y;
+            acc += da * da + db * db;
+            const float2 df = make_float2((float)da, (float)db);
+            reinterpret_cast<float2*>(r32_out + fbase)[q] = df;
+            reinterpret_cast<float2*>(d32 + fbase)[q] = df;
+        }
+    }
+    if (MODE == XI_INPLACE_RES || MODE == XI_ADD_R_RES || MODE == XI_DIFF) {
+        double s = block_sum(acc, red);
+        if (threadIdx.x == 0) partial[(long long)slot * gridDim.x + blockIdx.x] = s;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// y pass: Py consecutive kx columns of one (component, z) plane, length N along y
+// ---------------------------------------------------------------------------
+
+template <typename R, bool FWD>
+__global__ void __launch_bounds__(kThreads)
+k_y_pass(GridDesc g, unsigned mask, typename Cplx<R>::T* __restrict__ spec) {
+    using T2 = typename Cplx<R>::T;
+    const int slot = blockIdx.y;
+    if (!((mask >> slot) & 1u)) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int N = g.N, M = g.M, P = g.Py;
+    T2* b0 = reinterpret_cast<T2*>(smem_raw);
+    T2* b1 = b0 + N * P;
+    const int nkb = M / P;
+    const int kb = blockIdx.x % nkb;
+    const long long cz = blockIdx.x / nkb;                     // c*N + z
+    T2* base = spec + (long long)slot * 3 * g.NNM + cz * N * M + kb * P;
+    for (int q = threadIdx.x; q < N * P; q += blockDim.x) {
+        const int y = q / P, p = q - y * P;
+        b0[q] = base[(long long)y * M + p];
+    }
+    __syncthreads();
+    T2* res = fft_smem<FWD>(b0, b1, g.pN, TwTable<T2>::get(g), P, 1, P);
+    for (int q = threadIdx.x; q < N * P; q += blockDim.x) {
+        const int y = q / P, p = q - y * P;
+        base[(long long)y * M + p] = res[q];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// z pass: Pz consecutive kx columns at one ky, all three components, length N
+// along z.  Z_ITER: forward, tau_hat <- (I - 2P) tau_hat / N^3 (+ 2 k0 E at DC),
+// inverse.  Z_EQ: forward, then sum |xi . phi_hat|^2 / N^6 in FP64.
+// ---------------------------------------------------------------------------
+
+// Projector data of one (kx, ky, kz) mode: unnormalized direction m' (integers) with
+// the Nyquist rule applied.  Returns |m'|^2 (0 where P = 0).
+__device__ __forceinline__ int mode_dir(int kx, int my, int mz, int N, int* d) {
+    const int h = N / 2;
+    const int nyq_y = (my == h), nyq_z = (mz == h);
+    const int nx = (kx != 0), ny = (my != 0), nz = (mz != 0);
+    const int nonzero = nx + ny + nz;
+    const int nyqx = (kx == h);
+    d[0] = (nyqx && nonzero > 1) ? 0 : kx;
+    d[1] = (nyq_y && nonzero > 1) ? 0 : my;
+    d[2] = (nyq_z && nonzero > 1) ? 0 : mz;
+    return d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+}
+
+template <typename R, int MODE>
+__global__ void __launch_bounds__(kThreads)
+k_z_pass(GridDesc g, unsigned mask, typename Cplx<R>::T* __restrict__ spec, double* __restrict__ partial) {
+    using T2 = typename Cplx<R>::T;
+    const int slot = blockIdx.y;
+    if (!((mask >> slot) & 1u)) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int N = g.N, M = g.M, P = g.Pz, P3 = 3 * P;
+    T2* b0 = reinterpret_cast<T2*>(smem_raw);
+    T2* b1 = b0 + N * P3;
+    __shared__ double red[kThreads];
+    const int nkb = M / P;
+    const int kb = blockIdx.x % nkb;
+    const int ky = blockIdx.x / nkb;
+    T2* base = spec + (long long)slot * 3 * g.NNM + (long long)ky * M + kb * P;
+    // SMEM layout [z][c][p]: pencil c*P + p, index stride 3P
+    for (int q = threadIdx.x; q < N * P3; q += blockDim.x) {
+        const int z = q / P3, cp = q - z * P3, c = cp / P, p = cp - c * P;
+        b0[q] = base[(long long)c * g.NNM + (long long)z * N * M + p];
+    }
+    __syncthreads();
+    const T2* tw = TwTable<T2>::get(g);
+    T2* res = b0;
+    if (MODE != Z_INV) res = fft_smem<true>(b0, b1, g.pN, tw, P3, 1, P3);
+    T2* other = (res == b0) ? b1 : b0;
+
+    if (MODE == Z_ITER || MODE == Z_ITER_NOB || MODE == Z_EQ) {
+        const int my = signed_mode(ky, N);
+        const R scale = R(1.0 / (double)g.N3);
+        double acc = 0.0;
+        const double twopi_n = 6.283185307179586476925 / (double)N;
+        for (int q = threadIdx.x; q < N * P; q += blockDim.x) {
+            const int kz = q / P, p = q - kz * P;
+            const int kx = kb * P + p;
+            const int mz = signed_mode(kz, N);
+            T2* e = res + kz * P3 + p;
+            T2 s0 = e[0], s1 = e[P], s2 = e[2 * P];
+            const bool special = (kx == 0) && (ky == 0 || ky == N / 2) && (kz == 0 || kz == N / 2);
+            if (MODE == Z_EQ) {
+                if (!special) {
+                    int d[3];
+                    const int n2 = mode_dir(kx, my, mz, N, d);
+                    if (n2 > 0) {
+                        const double dr = d[0] * (double)s0.x + d[1] * (double)s1.x + d[2] * (double)s2.x;
+                        const double di = d[0] * (double)s0.y + d[1] * (double)s1.y + d[2] * (double)s2.y;
+                        acc += (kx == 0 ? 1.0 : 2.0) * (dr * dr + di * di);
+                    }
+                } else {
+                    // real part: plane kx = 0; imaginary part: plane kx = N/2
+                    int d[3];
+                    if (mode_dir(0, my, mz, N, d) > 0) {
+                        const double dr = d[0] * (double)s0.x + d[1] * (double)s1.x + d[2] * (double)s2.x;
+                        acc += dr * dr;
+                    }
+                    if (mode_dir(N / 2, my, mz, N, d) > 0) {
+                        const double di = d[0] * (double)s0.y + d[1] * (double)s1.y + d[2] * (double)s2.y;
+                        acc += di * di;
+                    }
+                }
+            } else {
+                T2 o0, o1, o2;
+                if (!special) {
+                    int d[3];
+                    const int n2 = mode_dir(kx, my, mz, N, d);
+                    // (I - 2P) s with P = d d^T / |d|^2 (n2 > 0 for every non-special mode)
+                    const R f = R(2.0) / R(n2);
+                    const T2 dot = mk(R(d[0]) * s0.x + R(d[1]) * s1.x + R(d[2]) * s2.x,
+                                      R(d[0]) * s0.y + R(d[1]) * s1.y + R(d[2]) * s2.y);
+                    o0 = mk(scale * (s0.x - f * R(d[0]) * dot.x), scale * (s0.y - f * R(d[0]) * dot.y));
+                    o1 = mk(scale * (s1.x - f * R(d[1]) * dot.x), scale * (s1.y - f * R(d[1]) * dot.y));
+                    o2 = mk(scale * (s2.x - f * R(d[2]) * dot.x), scale * (s2.y - f * R(d[2]) * dot.y));
+                } else {
+                    R a[3] = {s0.x, s1.x, s2.x};   // plane kx = 0
+                    R b[3] = {s0.y, s1.y, s2.y};   // plane kx = N/2
+                    int d[3];
+                    int n2 = mode_dir(0, my, mz, N, d);
+                    if (n2 > 0) {
+                        const R f = R(2.0) / R(n2);
+                        const R dot = R(d[0]) * a[0] + R(d[1]) * a[1] + R(d[2]) * a[2];
+                        for (int c = 0; c < 3; ++c) a[c] -= f * R(d[c]) * dot;
+                    }
+                    n2 = mode_dir(N / 2, my, mz, N, d);
+                    if (n2 > 0) {
+                        const R f = R(2.0) / R(n2);
+                        const R dot = R(d[0]) * b[0] + R(d[1]) * b[1] + R(d[2]) * b[2];
+                        for (int c = 0; c < 3; ++c) b[c] -= f * R(d[c]) * dot;
+                    }
+                    for (int c = 0; c < 3; ++c) {
+                        a[c] *= scale;
+                        b[c] *= scale;
+                    }
+                    if (MODE == Z_ITER && ky == 0 && kz == 0) {
+                        for (int c = 0; c < 3; ++c) a[c] += R(2.0 * g.k0 * g.E[slot][c]);
+                    }
+                    o0 = mk(a[0], b[0]);
+                    o1 = mk(a[1], b[1]);
+                    o2 = mk(a[2], b[2]);
+                }
+                e[0] = o0;
+                e[P] = o1;
+                e[2 * P] = o2;
+            }
+        }
+        if (MODE == Z_EQ) {
+            // |xi . phi_hat|^2 with xi = 2 pi m'/N and phi_hat = DFT/N^3
+            const double s = block_sum(acc, red) * twopi_n * twopi_n / ((double)g.N3 * (double)g.N3);
+            if (threadIdx.x == 0) partial[(long long)slot * gridDim.x + blockIdx.x] = s;
+            return;
+        }
+        __syncthreads();
+    }
+    if (MODE == Z_ITER || MODE == Z_ITER_NOB || MODE == Z_INV) {
+        if (MODE == Z_INV) other = b1;
+        res = fft_smem<false>(res, other, g.pN, tw, P3, 1, P3);
+    }
+    for (int q = threadIdx.x; q < N * P3; q += blockDim.x) {
+        const int z = q / P3, cp = q - z * P3, c = cp / P, p = cp - c * P;
+        base[(long long)c * g.NNM + (long long)z * N * M + p] = res[q];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// reductions and pointwise helpers
+// ---------------------------------------------------------------------------
+
+__global__ void k_reduce(const double* __restrict__ partial, int count, int groups, double* __restrict__ out) {
+    __shared__ double red[kThreads];
+    const int slot = blockIdx.x / groups, grp = blockIdx.x % groups;
+    const int per = count / groups;
+    const double* p = partial + (long long)slot * count + (long long)grp * per;
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < per; i += blockDim.x) acc += p[i];
+    double s = block_sum(acc, red);
+    if (threadIdx.x == 0) out[blockIdx.x] = s;
+}
+
+template <typename R>
+__global__ void k_init_tau(GridDesc g, unsigned mask, R* __restrict__ tau) {
+    const int slot = blockIdx.y;
+    if (!((mask >> slot) & 1u)) return;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < g.N3; i += (long long)gridDim.x * blockDim.x) {
+        const int ph = g.phase[i];
+        const double kp = ph == 0 ? g.KP[0] : (ph == 1 ? g.KP[1] : g.KP[2]);
+        for (int c = 0; c < 3; ++c) tau[((long long)slot * 3 + c) * g.N3 + i] = R(kp * g.E[slot][c]);
+    }
+}
+
+template <typename R>
+__global__ void k_e_to_tau(GridDesc g, int slot, const double* __restrict__ e, R* __restrict__ tau) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < g.N3; i += (long long)gridDim.x * blockDim.x) {
+        const int ph = g.phase[i];
+        const double kp = ph == 0 ? g.KP[0] : (ph == 1 ? g.KP[1] : g.KP[2]);
+        for (int c = 0; c < 3; ++c) tau[((long long)slot * 3 + c) * g.N3 + i] = R(kp * e[c * g.N3 + i]);
+    }
+}
+
+template <typename R>
+__global__ void k_tau_to_e(GridDesc g, int slot, const R* __restrict__ tau, double* __restrict__ e) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < g.N3; i += (long long)gridDim.x * blockDim.x) {
+        const int ph = g.phase[i];
+        const double kp = ph == 0 ? g.KP[0] : (ph == 1 ? g.KP[1] : g.KP[2]);
+        for (int c = 0; c < 3; ++c) e[c * g.N3 + i] = (double)tau[((long long)slot * 3 + c) * g.N3 + i] / kp;
+    }
+}
+
+__global__ void k_widen(GridDesc g, unsigned mask, const float* __restrict__ src, double* __restrict__ dst) {
+    const int slot = blockIdx.y;
+    if (!((mask >> slot) & 1u)) return;
+    const long long n = 3 * g.N3, off = (long long)slot * n;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        dst[off + i] = (double)src[off + i];
+}
+
+__global__ void k_axpy(GridDesc g, unsigned mask, const float* __restrict__ d, double* __restrict__ tau) {
+    const int slot = blockIdx.y;
+    if (!((mask >> slot) & 1u)) return;
+    const long long n = 3 * g.N3, off = (long long)slot * n;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        tau[off + i] += (double)d[off + i];
+}
+
+template <typename R>
+__global__ void k_convert(const double* __restrict__ s, R* __restrict__ d, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        d[i] = R(s[i]);
+}
+
+template <typename R>
+__global__ void k_convert_back(const R* __restrict__ s, double* __restrict__ d, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        d[i] = (double)s[i];
+}
+
+// ---------------------------------------------------------------------------
+// launch wrappers
+// ---------------------------------------------------------------------------
+
+static int pointwise_blocks(long long n) {
+    long long b = (n + kThreads - 1) / kThreads;
+    return (int)(b < 152 * 16 ? b : 152 * 16);
+}
+
+int x_ctas(const GridDesc& g) { return (int)(3 * g.NN / g.rows); }
+int z_ctas(const GridDesc& g) { return g.N * (g.M / g.Pz); }
+
+template <typename R, typename K>
+static void set_smem(K kern, size_t bytes) {
+    if (bytes > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+template <typename R>
+void launch_x_forward(const GridDesc& g, int mode, unsigned mask, const R* tau, void* spec,
+                      double* partial, cudaStream_t st) {
+    using T2 = typename Cplx<R>::T;
+    const size_t sm = 2ull * g.rows * g.M * sizeof(T2);
+    dim3 grid(x_ctas(g), g.nslots);
+    T2* sp = reinterpret_cast<T2*>(spec);
+    if (mode == XF_PLAIN) {
+        set_smem<R>(k_x_forward<R, XF_PLAIN>, sm);
+        k_x_forward<R, XF_PLAIN><<<grid, kThreads, sm, st>>>(g, mask, tau, sp, partial);
+    } else if (mode == XF_POLARIZE) {
+        set_smem<R>(k_x_forward<R, XF_POLARIZE>, sm);
+        k_x_forward<R, XF_POLARIZE><<<grid, kThreads, sm, st>>>(g, mask, tau, sp, partial);
+    } else {
+        set_smem<R>(k_x_forward<R, XF_FLUX>, sm);
+        k_x_forward<R, XF_FLUX><<<grid, kThreads, sm, st>>>(g, mask, tau, sp, partial);
+    }
+}
+
+template <typename R>
+void launch_y_pass(const GridDesc& g, bool forward, unsigned mask, void* spec, cudaStream_t st) {
+    using T2 = typename Cplx<R>::T;
+    const size_t sm = 2ull * g.N * g.Py * sizeof(T2);
+    dim3 grid(3 * g.N * (g.M / g.Py), g.nslots);
+    T2* sp = reinterpret_cast<T2*>(spec);
+    if (forward) {
+        set_smem<R>(k_y_pass<R, true>, sm);
+        k_y_pass<R, true><<<grid, kThreads, sm, st>>>(g, mask, sp);
+    } else {
+        set_smem<R>(k_y_pass<R, false>, sm);
+        k_y_pass<R, false><<<grid, kThreads, sm, st>>>(g, mask, sp);
+    }
+}
+
+template <typename R>
+void launch_z_pass(const GridDesc& g, int mode, unsigned mask, void* spec, double* partial, cudaStream_t st) {
+    using T2 = typename Cplx<R>::T;
+    const size_t sm = 2ull * 3 * g.N * g.Pz * sizeof(T2);
+    dim3 grid(z_ctas(g), g.nslots);
+    T2* sp = reinterpret_cast<T2*>(spec);
+    switch (mode) {
+        case Z_FWD:
+            set_smem<R>(k_z_pass<R, Z_FWD>, sm);
+            k_z_pass<R, Z_FWD><<<grid, kThreads, sm, st>>>(g, mask, sp, partial);
+            break;
+        case Z_INV:
+            set_smem<R>(k_z_pass<R, Z_INV>, sm);
+            k_z_pass<R, Z_INV><<<grid, kThreads, sm, st>>>(g, mask, sp, partial);
+            break;
+        case Z_ITER:
+            set_smem<R>(k_z_pass<R, Z_ITER>, sm);
+            k_z_pass<R, Z_ITER><<<grid, kThreads, sm, st>>>(g, mask, sp, partial);
+            break;
+        case Z_ITER_NOB:
+            set_smem<R>(k_z_pass<R, Z_ITER_NOB>, sm);
+            k_z_pass<R, Z_ITER_NOB><<<grid, kThreads, sm, st>>>(g, mask, sp, partial);
+            break;
+        default:
+            set_smem<R>(k_z_pass<R, Z_EQ>, sm);
+            k_z_pass<R, Z_EQ><<<grid, kThreads, sm, st>>>(g, mask, sp, partial);
+            break;
+    }
+}
+
+template <typename R>
+void launch_x_inverse(const GridDesc& g, int mode, unsigned mask, const void* spec, R* tau,
+                      const float* r32, float* d32, float* r32_out, double* partial, cudaStream_t st) {
+    using T2 = typename Cplx<R>::T;
+    const size_t sm = 2ull * g.rows * g.M * sizeof(T2);
+    dim3 grid(x_ctas(g), g.nslots);
+    const T2* sp = reinterpret_cast<const T2*>(spec);
+#define HMG_XI(MODE_)                                                                        \
+    set_smem<R>(k_x_inverse<R, MODE_>, sm);                                                  \
+    k_x_inverse<R, MODE_><<<grid, kThreads, sm, st>>>(g, mask, sp, tau, r32, d32, r32_out, partial)
+    switch (mode) {
+        case XI_PLAIN: HMG_XI(XI_PLAIN); break;
+        case XI_INPLACE: HMG_XI(XI_INPLACE); break;
+        case XI_INPLACE_RES: HMG_XI(XI_INPLACE_RES); break;
+        case XI_ADD_R_RES: HMG_XI(XI_ADD_R_RES); break;
+        default: HMG_XI(XI_DIFF); break;
+    }
+#undef HMG_XI
+}
+
+void launch_reduce(const double* partial, int nslots, int count, int groups, double* out, cudaStream_t st) {
+    k_reduce<<<nslots * groups, kThreads, 0, st>>>(partial, count, groups, out);
+}
+
+template <typename R>
+void launch_init_tau(const GridDesc& g, unsigned mask, R* tau, cudaStream_t st) {
+    k_init_tau<R><<<dim3(pointwise_blocks(g.N3), g.nslots), kThreads, 0, st>>>(g, mask, tau);
+}
+template <typename R>
+void launch_e_to_tau(const GridDesc& g, int slot, const double* e, R* tau, cudaStream_t st) {
+    k_e_to_tau<R><<<pointwise_blocks(g.N3), kThreads, 0, st>>>(g, slot, e, tau);
+}
+template <typename R>
+void launch_tau_to_e(const GridDesc& g, int slot, const R* tau, double* e, cudaStream_t st) {
+    k_tau_to_e<R><<<pointwise_blocks(g.N3), kThreads, 0, st>>>(g, slot, tau, e);
+}
+void launch_widen(const GridDesc& g, unsigned mask, const float* src, double* dst, cudaStream_t st) {
+    k_widen<<<dim3(pointwise_blocks(3 * g.N3), g.nslots), kThreads, 0, st>>>(g, mask, src, dst);
+}
+void launch_axpy(const GridDesc& g, unsigned mask, const float* d, double* tau, cudaStream_t st) {
+    k_axpy<<<dim3(pointwise_blocks(3 * g.N3), g.nslots), kThreads, 0, st>>>(g, mask, d, tau);
+}
+template <typename R>
+void launch_convert(const double* src, R* dst, long long n, cudaStream_t st) {
+    k_convert<R><<<pointwise_blocks(n), kThreads, 0, st>>>(src, dst, n);
+}
+template <typename R>
+void launch_convert_back(const R* src, double* dst, long long n, cudaStream_t st) {
+    k_convert_back<R><<<pointwise_blocks(n), kThreads, 0, st>>>(src, dst, n);
+}
+
+#define HMG_INST(R)                                                                                         \
+    template void launch_x_forward<R>(const GridDesc&, int, unsigned, const R*, void*, double*, cudaStream_t); \
+    template void launch_y_pass<R>(const GridDesc&, bool, unsigned, void*, cudaStream_t);                   \
+    template void launch_z_pass<R>(const GridDesc&, int, unsigned, void*, double*, cudaStream_t);           \
+    template void launch_x_inverse<R>(const GridDesc&, int, unsigned, const void*, R*, const float*, float*, \
+                                      float*, double*, cudaStream_t);                                       \
+    template void launch_init_tau<R>(const GridDesc&, unsigned, R*, cudaStream_t);                          \
+    template void launch_e_to_tau<R>(const GridDesc&, int, const double*, R*, cudaStream_t);                \
+    template void launch_tau_to_e<R>(const GridDesc&, int, const R*, double*, cudaStream_t);                \
+    template void launch_convert<R>(const double*, R*, long long, cudaStream_t);                            \
+    template void launch_convert_back<R>(const R*, double*, long long, cudaStream_t);
+HMG_INST(float)
+HMG_INST(double)
+#undef HMG_INST
+
+}  // namespace hmg

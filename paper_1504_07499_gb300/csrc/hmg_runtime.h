@@ -1,0 +1,120 @@
+// Host-side runtime objects of libhmg (contexts, plans, solve state, solver driver).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/hmg.h"
+#include "hmg_internal.h"
+
+namespace hmg {
+
+void set_error(const char* fmt, ...);
+extern thread_local std::string g_last_error;
+
+bool valid_length(int L);
+bool valid_N(int N);
+bool is_device_ptr(const void* p);
+cudaError_t copy_in(void* dst_dev, const void* src, size_t bytes, cudaStream_t st);
+cudaError_t copy_out(void* dst, const void* src_dev, size_t bytes, cudaStream_t st);
+size_t state_bytes(int N, bool fp64, int nslots);
+
+// FFT schedules and twiddle tables of one grid size.
+struct GridPlan {
+    int N = 0;
+    FftPlan pN{}, pM{};
+    float2* tw32 = nullptr;
+    double2* tw64 = nullptr;
+    ~GridPlan();
+};
+
+// Device fields of one solve: tau64/spec64 (FP64 master), f32buf/r32/spec32 (FP32 bulk).
+struct SolveState {
+    int N = 0;
+    bool fp64 = true;
+    int nslots = 0;
+    uint8_t* phase = nullptr;
+    double* tau64 = nullptr;
+    void* spec64 = nullptr;
+    float* f32buf = nullptr;
+    float* r32 = nullptr;
+    void* spec32 = nullptr;
+    double* partial = nullptr;
+    double* partial2 = nullptr;
+    double* red = nullptr;   // [0,16): sweep sums, [16,32): flux sums, [32,48): eq sums
+    bool ensure(::hmg_ctx* c, int N, bool fp64, int nslots);
+    void free_all(::hmg_ctx* c);
+};
+
+GridDesc make_desc(const GridPlan& gp, bool fp64, const double k[3], const uint8_t* phase_d, int nslots);
+
+// Per-kernel CUDA-event timing of the solver's launches.
+struct Tracer {
+    bool on = false;
+    double ms[HMG_K_COUNT] = {0};
+    long long launches[HMG_K_COUNT] = {0};
+    double bytes[HMG_K_COUNT] = {0};
+    struct Pending {
+        int kind;
+        int ev;
+        double bytes;
+    };
+    std::vector<cudaEvent_t> events;   // pairs (start, stop)
+    std::vector<int> free_pairs;
+    std::vector<Pending> pending;
+    int begin(cudaStream_t st);
+    void end(int ev, int kind, double bytes, cudaStream_t st);
+    void collect();                    // after a stream synchronize
+    void reset();
+    ~Tracer();
+};
+
+// Driver of one solve on one SolveState.
+struct Solver {
+    GridDesc g;
+    SolveState* s;
+    cudaStream_t st;
+    Tracer* tr = nullptr;
+    template <typename R>
+    void sweep(unsigned mask, R* field, void* spec, int zmode, int ximode, const float* r32in, float* d32,
+               float* r32out);
+    template <typename R>
+    void equilibrium(unsigned mask, const R* field, void* spec);
+    template <typename R>
+    bool check_eq(unsigned mask, const R* field, void* spec, double eps_eq[3], double flux[3][3]);
+    bool fetch(double* h, int off, int count);
+    double eps_from_sum(double sum, int slot) const;
+    hmg_status run_fp64(int max_iter, double tol, hmg_info* info, double K[9]);
+    hmg_status run_bulk(int max_iter, double tol, hmg_info* info, double K[9]);
+    hmg_status finish(const int status[3], const int iters[3], const int it64[3], const double eps_comp[3],
+                      const double eps_eq[3], const double flux[3][3], int rounds, hmg_info* info, double K[9]);
+};
+
+struct Request;
+struct Server;
+
+}  // namespace hmg
+
+struct hmg_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    size_t budget = 0;
+    size_t used = 0;
+    std::map<void*, size_t> sizes;
+    std::map<int, std::shared_ptr<hmg::GridPlan>> plans;
+    hmg::SolveState solve;
+    std::shared_ptr<hmg::GridPlan> plan(int N);
+    void* alloc(size_t bytes);
+    void release(void* p);
+    hmg::Server* server = nullptr;
+    hmg::Tracer tracer;
+};
+
+namespace hmg {
+using Context = ::hmg_ctx;
+}  // namespace hmg

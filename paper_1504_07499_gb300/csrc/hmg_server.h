@@ -1,0 +1,47 @@
+// Request loop behind hmg_submit / hmg_poll.
+#pragma once
+
+#include <condition_variable>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <thread>
+#include <vector>
+
+#include "../../include/hmg.h"
+
+namespace hmg {
+
+struct Request {
+    uint64_t ticket = 0;
+    std::vector<uint8_t> phase;
+    int N = 0;
+    double k[3] = {0, 0, 0};
+    double tol = 0;
+    hmg_precision prec = HMG_FP64;
+    hmg_status status = HMG_PENDING;
+    double K[9] = {0};
+    hmg_info info{};
+    double t_submit = 0, t_start = 0, t_done = 0;
+};
+
+struct Server {
+    explicit Server(int device, size_t budget);
+    ~Server();
+    hmg_status submit(const uint8_t* phase, int N, const double k[3], double tol, hmg_precision p, uint64_t* ticket);
+    hmg_status poll(uint64_t ticket, double K[9], hmg_info* info);
+
+   private:
+    void loop();
+    int device;
+    size_t budget;
+    std::mutex mu;
+    std::condition_variable cv;
+    std::deque<uint64_t> queue;
+    std::map<uint64_t, Request> reqs;
+    uint64_t next = 1;
+    bool stop = false;
+    std::thread worker;
+};
+
+}  // namespace hmg

@@ -1,0 +1,269 @@
+"""Python binding of libhmg (include/hmg.h): argument marshalling only.
+
+Every function here has the name of the C entry point it calls and does no
+arithmetic of the method itself: arrays are passed as raw pointers (numpy arrays
+as host pointers, torch CUDA tensors as device pointers) and results come back in
+caller-provided buffers.  The CUDA library must be built (``build.build()``);
+importing a function that needs it raises if libhmg.so is missing -- there is no
+CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libhmg.so")
+
+HMG_OK, HMG_PENDING = 0, 1
+HMG_INVALID_ARG, HMG_OUT_OF_MEMORY, HMG_NOT_CONVERGED = -1, -2, -3
+HMG_DIVERGED, HMG_CUDA_ERROR, HMG_BUSY, HMG_UNKNOWN_TICKET = -4, -5, -6, -7
+HMG_FP64, HMG_FP32_BULK = 0, 1
+STATUS_NAMES = {0: "OK", 1: "PENDING", -1: "INVALID_ARG", -2: "OUT_OF_MEMORY", -3: "NOT_CONVERGED",
+                -4: "DIVERGED", -5: "CUDA_ERROR", -6: "BUSY", -7: "UNKNOWN_TICKET"}
+
+# every symbol include/hmg.h declares
+EXPORTS = ["hmg_version", "hmg_last_error", "hmg_create", "hmg_destroy", "hmg_voxelize", "hmg_solve",
+           "hmg_solve_fields", "hmg_em_iterate", "hmg_equilibrium", "hmg_fft_forward", "hmg_fft_inverse",
+           "hmg_solve_batch", "hmg_submit", "hmg_poll", "hmg_footprint", "hmg_trace_enable",
+           "hmg_trace_read"]
+KERNEL_KINDS = ["x_forward", "y_forward", "z_green", "y_inverse", "x_inverse", "eq_x", "eq_z", "other"]
+
+
+class hmg_sphere(C.Structure):
+    _fields_ = [("cx", C.c_double), ("cy", C.c_double), ("cz", C.c_double), ("r", C.c_double)]
+
+
+class hmg_info(C.Structure):
+    _fields_ = [("iters", C.c_int * 3), ("iters_fp64", C.c_int * 3), ("eps_comp", C.c_double * 3),
+                ("eps_eq", C.c_double * 3), ("seconds", C.c_double), ("fp64_rounds", C.c_int),
+                ("status", C.c_int * 3)]
+
+    def as_dict(self) -> dict:
+        return dict(iters=list(self.iters), iters_fp64=list(self.iters_fp64), eps_comp=list(self.eps_comp),
+                    eps_eq=list(self.eps_eq), seconds=self.seconds, fp64_rounds=self.fp64_rounds,
+                    status=[STATUS_NAMES.get(s, s) for s in self.status])
+
+
+class HmgError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def lib() -> C.CDLL:
+    """The loaded libhmg.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"libhmg.so not built ({LIB_PATH}); run paper_1504_07499_gb300.build.build()")
+        L = C.CDLL(LIB_PATH)
+        vp, i, d, sz = C.c_void_p, C.c_int, C.c_double, C.c_size_t
+        dp = C.POINTER(C.c_double)
+        L.hmg_version.restype = C.c_char_p
+        L.hmg_last_error.restype = C.c_char_p
+        L.hmg_create.argtypes = [C.POINTER(vp), i, sz]
+        L.hmg_destroy.argtypes = [vp]
+        L.hmg_voxelize.argtypes = [vp, vp, sz, d, i, vp]
+        L.hmg_solve.argtypes = [vp, vp, i, d, d, d, d, i, i, dp, C.POINTER(hmg_info)]
+        L.hmg_solve_fields.argtypes = [vp, vp, i, d, d, d, d, i, i, dp, C.POINTER(hmg_info), vp]
+        L.hmg_em_iterate.argtypes = [vp, vp, i, d, d, d, dp, i, i, vp, dp]
+        L.hmg_equilibrium.argtypes = [vp, vp, i, d, d, d, i, vp, dp, dp]
+        L.hmg_fft_forward.argtypes = [vp, i, i, i, vp, vp]
+        L.hmg_fft_inverse.argtypes = [vp, i, i, i, vp, vp]
+        L.hmg_solve_batch.argtypes = [vp, i, C.POINTER(vp), C.POINTER(i), dp, d, i, i, dp, C.POINTER(hmg_info)]
+        L.hmg_submit.argtypes = [vp, vp, i, d, d, d, d, i, C.POINTER(C.c_uint64)]
+        L.hmg_poll.argtypes = [vp, C.c_uint64, dp, C.POINTER(hmg_info)]
+        L.hmg_trace_enable.argtypes = [vp, i]
+        L.hmg_trace_read.argtypes = [vp, i, dp, C.POINTER(C.c_longlong), dp]
+        L.hmg_footprint.argtypes = [i, i]
+        L.hmg_footprint.restype = sz
+        for name in EXPORTS:
+            if name not in ("hmg_version", "hmg_last_error", "hmg_footprint"):
+                getattr(L, name).restype = C.c_int
+        _lib = L
+    return _lib
+
+
+def _ptr(a) -> int:
+    """Raw address of a numpy array (host) or torch tensor (host or device)."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return a.data_ptr()
+    if not a.flags["C_CONTIGUOUS"]:
+        raise ValueError("array must be C-contiguous")
+    return a.ctypes.data
+
+
+def _check(status: int, allow=(HMG_OK,)) -> int:
+    if status not in allow:
+        raise HmgError(status, lib().hmg_last_error().decode())
+    return status
+
+
+def _dbuf(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+# --- C entry points ------------------------------------------------------------
+
+def hmg_version() -> str:
+    return lib().hmg_version().decode()
+
+
+def hmg_last_error() -> str:
+    return lib().hmg_last_error().decode()
+
+
+def hmg_footprint(N: int, precision: int = HMG_FP32_BULK) -> int:
+    return lib().hmg_footprint(N, precision)
+
+
+def hmg_create(device: int = 0, budget: int = 0) -> int:
+    h = C.c_void_p()
+    _check(lib().hmg_create(C.byref(h), device, budget))
+    return h.value
+
+
+def hmg_destroy(ctx: int) -> None:
+    _check(lib().hmg_destroy(ctx))
+
+
+def hmg_voxelize(ctx: int, spheres, layer: float, N: int, phase_out) -> None:
+    """spheres: (n, 4) float64 array (cx, cy, cz, r) or device tensor; phase_out: N^3 uint8."""
+    n = spheres.shape[0]
+    _check(lib().hmg_voxelize(ctx, _ptr(spheres), n, layer, N, _ptr(phase_out)))
+
+
+def hmg_solve(ctx: int, phase, N: int, k, tol: float, precision: int, max_iter: int = 0,
+              allow=(HMG_OK,)):
+    K = np.zeros(9)
+    info = hmg_info()
+    st = lib().hmg_solve(ctx, _ptr(phase), N, k[0], k[1], k[2], tol, precision, max_iter, _dbuf(K), C.byref(info))
+    _check(st, allow)
+    return K.reshape(3, 3), info.as_dict(), st
+
+
+def hmg_solve_fields(ctx: int, phase, N: int, k, tol: float, precision: int, e_out, max_iter: int = 0,
+                     allow=(HMG_OK,)):
+    K = np.zeros(9)
+    info = hmg_info()
+    st = lib().hmg_solve_fields(ctx, _ptr(phase), N, k[0], k[1], k[2], tol, precision, max_iter, _dbuf(K),
+                                C.byref(info), _ptr(e_out))
+    _check(st, allow)
+    return K.reshape(3, 3), info.as_dict(), st
+
+
+def hmg_em_iterate(ctx: int, phase, N: int, k, grad_Theta, precision: int, n_iter: int, e_inout):
+    g = np.ascontiguousarray(grad_Theta, dtype=np.float64)
+    eps = np.zeros(max(n_iter, 1))
+    _check(lib().hmg_em_iterate(ctx, _ptr(phase), N, k[0], k[1], k[2], _dbuf(g), precision, n_iter,
+                                _ptr(e_inout), _dbuf(eps)))
+    return eps[:n_iter]
+
+
+def hmg_equilibrium(ctx: int, phase, N: int, k, precision: int, e):
+    eps = np.zeros(1)
+    flux = np.zeros(3)
+    _check(lib().hmg_equilibrium(ctx, _ptr(phase), N, k[0], k[1], k[2], precision, _ptr(e), _dbuf(eps),
+                                 _dbuf(flux)))
+    return float(eps[0]), flux
+
+
+def hmg_fft_forward(ctx: int, N: int, count: int, precision: int, x, X_out) -> None:
+    _check(lib().hmg_fft_forward(ctx, N, count, precision, _ptr(x), _ptr(X_out)))
+
+
+def hmg_fft_inverse(ctx: int, N: int, count: int, precision: int, X, x_out) -> None:
+    _check(lib().hmg_fft_inverse(ctx, N, count, precision, _ptr(X), _ptr(x_out)))
+
+
+def hmg_solve_batch(ctx: int, phases, N_list, k3, tol: float, precision: int, max_iter: int = 0,
+                    allow=(HMG_OK,)):
+    n = len(phases)
+    ptrs = (C.c_void_p * n)(*[_ptr(p) for p in phases])
+    Ns = (C.c_int * n)(*N_list)
+    kk = np.ascontiguousarray(k3, dtype=np.float64).reshape(-1)
+    K = np.zeros(9 * n)
+    infos = (hmg_info * n)()
+    st = lib().hmg_solve_batch(ctx, n, ptrs, Ns, _dbuf(kk), tol, precision, max_iter, _dbuf(K), infos)
+    _check(st, allow)
+    return K.reshape(n, 3, 3), [x.as_dict() for x in infos], st
+
+
+def hmg_submit(ctx: int, phase, N: int, k, tol: float, precision: int) -> int:
+    t = C.c_uint64()
+    _check(lib().hmg_submit(ctx, _ptr(phase), N, k[0], k[1], k[2], tol, precision, C.byref(t)))
+    return t.value
+
+
+def hmg_poll(ctx: int, ticket: int):
+    """Returns (status, K 3x3 or None, info dict or None)."""
+    K = np.zeros(9)
+    info = hmg_info()
+    st = lib().hmg_poll(ctx, ticket, _dbuf(K), C.byref(info))
+    if st == HMG_PENDING:
+        return st, None, None
+    _check(st, (HMG_OK, HMG_NOT_CONVERGED, HMG_DIVERGED))
+    return st, K.reshape(3, 3), info.as_dict()
+
+
+def hmg_trace_enable(ctx: int, enable: bool) -> None:
+    _check(lib().hmg_trace_enable(ctx, 1 if enable else 0))
+
+
+def hmg_trace_read(ctx: int) -> dict:
+    """{kind name: (total ms, launches, algorithmic bytes)} for every kernel kind."""
+    out = {}
+    for k, name in enumerate(KERNEL_KINDS):
+        ms, n, b = np.zeros(1), C.c_longlong(), np.zeros(1)
+        _check(lib().hmg_trace_read(ctx, k, _dbuf(ms), C.byref(n), _dbuf(b)))
+        out[name] = (float(ms[0]), int(n.value), float(b[0]))
+    return out
+
+
+@dataclass
+class Context:
+    """Owns one hmg context; a thin convenience wrapper over the functions above."""
+    device: int = 0
+    budget: int = 0
+
+    def __post_init__(self):
+        self.handle = hmg_create(self.device, self.budget)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            hmg_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def voxelize(self, spheres, layer: float, N: int, out=None):
+        sph = np.ascontiguousarray(spheres, dtype=np.float64) if not hasattr(spheres, "data_ptr") else spheres
+        if out is None:
+            out = np.empty((N, N, N), dtype=np.uint8)
+        hmg_voxelize(self.handle, sph, layer, N, out)
+        return out
+
+    def solve(self, phase, k, tol=1e-8, precision=HMG_FP64, max_iter=0, allow=(HMG_OK,)):
+        N = phase.shape[-1]
+        return hmg_solve(self.handle, phase, N, k, tol, precision, max_iter, allow)
