@@ -1,0 +1,361 @@
+"""Benchmark: full Eyre-Milton solves of a 256^3 three-phase RVE on one GB300 (or N replicas).
+
+One step = voxelize the RVE's sphere list (device-resident) and solve the cell problem
+for the three unit gradients to tol 1e-8 (eps_comp and eps_eq), returning K.
+Workload: 100 identical non-overlapping spheres at 40 % volume fraction (seeded
+RSA + growth sweeps), layer l = 0.3, conductivities 0.20 / 0.25 / 400 (contrast 2000).
+
+value  = voxel-iterations/s = sum over steps of N^3 * (sweeps over the 3 gradients) / time,
+         inputs resident in HBM, device time from CUDA events around the K timed steps,
+         max over ranks; fields (1.4 GB) are far larger than L2, so no flush is needed.
+e2e    = the same metric through the public C ABI with host buffers: the sphere list
+         and the phase grid cross host<->device inside every step.
+Multi-GPU: independent replicas (one RVE per rank, seed 3000 + rank), weak scaling.
+
+--impl reference times the CPU oracle (the FP64 numpy/scipy implementation written from
+the paper) on the host cores, on bounded samples of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_GRID = 256
+N_SPHERES, F_SP, LAYER, SEED = 100, 0.40, 0.3, 3000
+K_PHASES = (0.20, 0.25, 400.0)
+TOL = 1e-8
+METRIC = "voxel-iterations/s at 256^3 (3 unit gradients, tol 1e-8)"
+UNIT = "voxel-iter/s"
+
+
+def workload_config(precision: str) -> dict:
+    return {"workload": "rsa256: 256^3 RVE, 100 spheres at 40% (RSA + growth sweeps), layer 0.3, "
+                        "k 0.20/0.25/400 (contrast 2000), tol 1e-8, 3 unit gradients",
+            "N": N_GRID, "n_spheres": N_SPHERES, "f_sp": F_SP, "layer": LAYER, "k": list(K_PHASES),
+            "tol": TOL, "precision": precision, "seed": SEED,
+            "l2": "inputs larger than L2 (solver fields 1.4 GB vs 129 MB L2), no flush"}
+
+
+def measured_peaks() -> dict:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh)
+    except OSError:
+        return {}
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.lines: list[str] = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing (reference arm and cpu_baseline)
+# ---------------------------------------------------------------------------
+
+def oracle_phase(spheres):
+    from oracle import em as om
+    return om.voxelize(spheres, LAYER, N_GRID)
+
+
+def oracle_sample(ph, sweeps: int = 1) -> dict:
+    """Time `sweeps` oracle sweeps (steps 2-7) of one gradient on the 256^3 RVE."""
+    from oracle import em as om
+    t0 = time.perf_counter()
+    om.em_solve(ph, K_PHASES, (1.0, 0.0, 0.0), tol=0.0, max_iter=sweeps)
+    dt = time.perf_counter() - t0
+    return {"seconds": dt, "voxel_iters": sweeps * N_GRID ** 3, "threads": om._workers()}
+
+
+def run_reference(args) -> None:
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from paper_1504_07499_gb300 import inputs as I
+    ph = oracle_phase(I.generate_spheres(SEED, N_SPHERES, F_SP).spheres)
+    for _ in range(args.warmup):
+        oracle_sample(ph, 1)
+    tot_t, tot_v, thr = 0.0, 0, 1
+    for _ in range(args.steps):
+        r = oracle_sample(ph, 1)
+        tot_t += r["seconds"]
+        tot_v += r["voxel_iters"]
+        thr = r["threads"]
+    value = tot_v / tot_t
+    sample = "one oracle sweep (steps 2-7, one gradient) of the 256^3 RVE per step"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": workload_config("fp64 (CPU oracle)"),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": thr, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+def main() -> None:
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="hmg", choices=["hmg", "reference"])
+    ap.add_argument("--precision", default="fp32bulk", choices=["fp32bulk", "fp64"])
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison solve")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--sweeps-only", type=int, default=0,
+                    help="profiling case: voxelize, run this many sweeps of one gradient, exit")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import torch
+    import torch.distributed as dist
+
+    from paper_1504_07499_gb300 import build, hmg, inputs as I
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if rank == 0 or world == 1:
+        build.build()
+    if world > 1:
+        dist.barrier()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    prec = hmg.HMG_FP32_BULK if args.precision == "fp32bulk" else hmg.HMG_FP64
+    ctx = hmg.Context(local)
+    seed = SEED + rank
+    sl = I.generate_spheres(seed, N_SPHERES, F_SP)
+    sph_d = torch.from_numpy(np.ascontiguousarray(sl.spheres)).cuda()
+    phase_d = torch.empty(N_GRID ** 3, dtype=torch.uint8, device="cuda")
+    N3 = N_GRID ** 3
+
+    def step():
+        hmg.hmg_voxelize(ctx.handle, sph_d, LAYER, N_GRID, phase_d)
+        _, info, _ = hmg.hmg_solve(ctx.handle, phase_d, N_GRID, K_PHASES, TOL, prec)
+        return info
+
+    if args.sweeps_only:
+        hmg.hmg_voxelize(ctx.handle, sph_d, LAYER, N_GRID, phase_d)
+        e = torch.zeros((3, N3), dtype=torch.float64, device="cuda")
+        e[0] = 1.0
+        hmg.hmg_em_iterate(ctx.handle, phase_d, N_GRID, K_PHASES, (1.0, 0.0, 0.0), prec, args.sweeps_only, e)
+        torch.cuda.synchronize()
+        ctx.close()
+        return
+
+    for _ in range(args.warmup):
+        step()
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    hmg.hmg_trace_enable(ctx.handle, True)
+    barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    sweeps, lat = 0, []
+    for _ in range(args.steps):
+        t = time.perf_counter()
+        info = step()
+        lat.append(time.perf_counter() - t)
+        sweeps += sum(info["iters"])
+    ev1.record()
+    torch.cuda.synchronize()
+    barrier()
+    ms = ev0.elapsed_time(ev1)
+    hmg.hmg_trace_enable(ctx.handle, False)
+    trace = hmg.hmg_trace_read(ctx.handle)
+    clocks = sampler.stop()
+
+    tot = torch.tensor([ms, float(sweeps * N3)], dtype=torch.float64, device="cuda")
+    if world > 1:
+        t_max = tot[:1].clone()
+        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
+        vox = tot[1:].clone()
+        dist.all_reduce(vox, op=dist.ReduceOp.SUM)
+        ms_max, vox_all = float(t_max.item()), float(vox.item())
+    else:
+        ms_max, vox_all = ms, float(sweeps * N3)
+    value = vox_all / (ms_max / 1e3)
+
+    # --- end to end through the C ABI with host buffers ---------------------------
+    sph_h = torch.from_numpy(np.ascontiguousarray(sl.spheres)).pin_memory().numpy()
+    phase_h = torch.empty(N3, dtype=torch.uint8).pin_memory().numpy()
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e2e_sweeps = 0
+    for _ in range(args.e2e_steps):
+        hmg.hmg_voxelize(ctx.handle, sph_h, LAYER, N_GRID, phase_h)               # D2H phase grid
+        K, info, _ = hmg.hmg_solve(ctx.handle, phase_h, N_GRID, K_PHASES, TOL, prec)  # H2D phase, D2H K
+        e2e_sweeps += sum(info["iters"])
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    e2e_t = torch.tensor([e2e_s, float(e2e_sweeps * N3)], dtype=torch.float64, device="cuda")
+    if world > 1:
+        a = e2e_t[:1].clone()
+        dist.all_reduce(a, op=dist.ReduceOp.MAX)
+        b = e2e_t[1:].clone()
+        dist.all_reduce(b, op=dist.ReduceOp.SUM)
+        e2e_s, e2e_vox = float(a.item()), float(b.item())
+    else:
+        e2e_vox = float(e2e_sweeps * N3)
+    h2d = sl.spheres.nbytes + N3
+    d2h = N3 + 9 * 8
+
+    if rank != 0:
+        if world > 1:
+            dist.barrier()
+            dist.destroy_process_group()
+        ctx.close()
+        return
+
+    # --- roofline of the dominant kernel -------------------------------------------
+    peaks = measured_peaks()
+    peak = peaks.get("hbm_gbs")
+    peak_src = "measured" if peak else "fallback"
+    if not peak:
+        peak = 6800.0
+    kinds = {k: v for k, v in trace.items() if v[1] > 0}
+    total_ms = sum(v[0] for v in kinds.values())
+    dom = max((k for k in kinds if k != "other"), key=lambda k: kinds[k][0])
+    d_ms, d_n, d_bytes = kinds[dom]
+    achieved = (d_bytes / d_n) / (d_ms / d_n / 1e3) / 1e9
+    traffic = None
+    try:
+        with open(os.path.join(ROOT, "profiles", "ncu_traffic.json")) as fh:
+            tinfo = json.load(fh)
+        ent = tinfo.get(args.precision, {}).get(dom)
+        if ent and ent.get("source_sha") == _kernel_sha():
+            traffic = ent["dram_bytes_per_launch"]
+    except (OSError, ValueError):
+        pass
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": traffic, "peak_source": peak_src,
+                "algo_bytes_per_launch": d_bytes / d_n, "avg_launch_ms": d_ms / d_n}
+    # whole-sweep algorithmic fraction: 25 B (FP32) / 49 B (FP64) per voxel-iteration
+    per_vox = 25.0 if prec == hmg.HMG_FP32_BULK else 49.0
+    kernels = {k: {"ms": v[0], "launches": v[1], "share": v[0] / total_ms,
+                   "GBps": (v[2] / (v[0] / 1e3) / 1e9) if v[0] > 0 and v[2] > 0 else None}
+               for k, v in kinds.items()}
+    launches = int(sum(v[1] for v in kinds.values()))
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if prec == hmg.HMG_FP32_BULK else "f64", "data": "synthetic",
+            "config": workload_config(args.precision),
+            "solves_per_s": world * args.steps / (ms_max / 1e3),
+            "latency_ms": {"p50": 1e3 * float(np.percentile(lat, 50)), "p99": 1e3 * float(np.percentile(lat, 99))},
+            "sweeps_per_solve": sweeps / args.steps,
+            "roofline": roofline,
+            "algorithmic_hbm_frac": value / world * per_vox / (peak * 1e9),
+            "kernels": kernels,
+            "gpu_launches": launches,
+            "clocks": clocks,
+            "e2e": {"value": e2e_vox / e2e_s if e2e_vox else None, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}}
+
+    if not args.no_fp64 and prec == hmg.HMG_FP32_BULK:
+        t = time.perf_counter()
+        _, info64, _ = hmg.hmg_solve(ctx.handle, phase_d, N_GRID, K_PHASES, TOL, hmg.HMG_FP64)
+        dt = time.perf_counter() - t
+        sw = sum(info64["iters"])
+        line["fp64_plain"] = {"voxel_iter_per_s": sw * N3 / dt, "solve_s": dt, "sweeps": sw,
+                              "speedup_fp32bulk_solves": dt / (ms_max / 1e3 / args.steps)}
+    if not args.no_cpu and world == 1:
+        r = oracle_sample(oracle_phase(sl.spheres), 2)
+        line["cpu_baseline"] = {"value": r["voxel_iters"] / r["seconds"], "unit": UNIT, "cores": r["threads"],
+                                "kind": "oracle",
+                                "sample": "2 oracle sweeps (steps 2-7, one gradient) of the 256^3 RVE, FP64"}
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    ctx.close()
+
+
+def _kernel_sha() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1504_07499_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(csrc, f), "rb") as fh:
+                h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+if __name__ == "__main__":
+    main()

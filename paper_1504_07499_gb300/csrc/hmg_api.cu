@@ -391,7 +391,7 @@ bool Solver::check_eq(unsigned mask, const R* field, void* spec, double eps_eq[3
 // Plain FP64 method: the Algorithm of §3 in its printed order.
 hmg_status Solver::run_fp64(int max_iter, double tol, hmg_info* info, double K[9]) {
     const unsigned all = (1u << g.nslots) - 1u;
-    launch_init_tau<double>(g, all, s->tau64, st);
+    HMG_TRACED(HMG_K_OTHER, 0.0, launch_init_tau<double>(g, all, s->tau64, st));
     double eps_comp[3] = {INFINITY, INFINITY, INFINITY}, eps_eq[3] = {INFINITY, INFINITY, INFINITY};
     double flux[3][3] = {};
     int iters[3] = {0, 0, 0}, status[3] = {HMG_NOT_CONVERGED, HMG_NOT_CONVERGED, HMG_NOT_CONVERGED};
@@ -436,7 +436,7 @@ hmg_status Solver::run_fp64(int max_iter, double tol, hmg_info* info, double K[9
 hmg_status Solver::run_bulk(int max_iter, double tol, hmg_info* info, double K[9]) {
     enum { PH_A = 0, PH_OUTER = 1, PH_INNER = 2, PH_DONE = 3 };
     const unsigned all = (1u << g.nslots) - 1u;
-    launch_init_tau<float>(g, all, s->f32buf, st);
+    HMG_TRACED(HMG_K_OTHER, 0.0, launch_init_tau<float>(g, all, s->f32buf, st));
     int state[3], iters[3] = {0, 0, 0}, it64[3] = {0, 0, 0}, status[3];
     double eps_comp[3] = {INFINITY, INFINITY, INFINITY}, eps_eq[3] = {INFINITY, INFINITY, INFINITY};
     double eps32[3] = {INFINITY, INFINITY, INFINITY}, best[3], outer_eps[3] = {INFINITY, INFINITY, INFINITY};
@@ -531,16 +531,16 @@ hmg_status Solver::run_bulk(int max_iter, double tol, hmg_info* info, double K[9
                 if (eps32[sl] < eta * outer_eps[sl] || since_best[sl] >= stall) to_outer_i |= 1u << sl;
             }
         }
-        if (to_outer_a) launch_widen(g, to_outer_a, s->f32buf, s->tau64, st);
-        if (to_outer_i) launch_axpy(g, to_outer_i, s->f32buf, s->tau64, st);
+        if (to_outer_a) HMG_TRACED(HMG_K_OTHER, 0.0, launch_widen(g, to_outer_a, s->f32buf, s->tau64, st));
+        if (to_outer_i) HMG_TRACED(HMG_K_OTHER, 0.0, launch_axpy(g, to_outer_i, s->f32buf, s->tau64, st));
         for (int sl = 0; sl < g.nslots; ++sl)
             if (((to_outer_a | to_outer_i) >> sl) & 1u) state[sl] = PH_OUTER;
     }
     unsigned left = 0;
     for (int sl = 0; sl < g.nslots; ++sl)
         if (status[sl] == HMG_NOT_CONVERGED) {
-            if (state[sl] == PH_A) launch_widen(g, 1u << sl, s->f32buf, s->tau64, st);
-            if (state[sl] == PH_INNER) launch_axpy(g, 1u << sl, s->f32buf, s->tau64, st);
+            if (state[sl] == PH_A) HMG_TRACED(HMG_K_OTHER, 0.0, launch_widen(g, 1u << sl, s->f32buf, s->tau64, st));
+            if (state[sl] == PH_INNER) HMG_TRACED(HMG_K_OTHER, 0.0, launch_axpy(g, 1u << sl, s->f32buf, s->tau64, st));
             left |= 1u << sl;
         }
     if (left && !check_eq<double>(left, s->tau64, s->spec64, eps_eq, flux)) return HMG_CUDA_ERROR;

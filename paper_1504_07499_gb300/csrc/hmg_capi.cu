@@ -244,7 +244,9 @@ hmg_status hmg_voxelize(hmg_ctx* ctx, const hmg_sphere* spheres, size_t n, doubl
     }
     cudaMemcpyAsync(qd, q.data(), q.size() * sizeof(long long), cudaMemcpyHostToDevice, ctx->stream);
     uint8_t* dst = dev_out ? phase_out : tmp;
+    const int ev = ctx->tracer.on ? ctx->tracer.begin(ctx->stream) : -1;
     launch_voxelize(qd, (int)n, N, S, dst, ctx->stream);
+    if (ev >= 0) ctx->tracer.end(ev, HMG_K_OTHER, (double)N3, ctx->stream);
     if (!dev_out) cudaMemcpyAsync(phase_out, tmp, N3, cudaMemcpyDeviceToHost, ctx->stream);
     st = check_launch(ctx, "voxelize");
     cudaFree(qd);
