@@ -162,6 +162,32 @@ hmg_status hmg_fft_forward(hmg_ctx* ctx, int N, int count, hmg_precision precisi
 hmg_status hmg_fft_inverse(hmg_ctx* ctx, int N, int count, hmg_precision precision,
                            const double* X, double* x_out);
 
+/* Largest N accepted by hmg_equilibrium_noalloc. */
+#define HMG_NOALLOC_MAX_N 64
+
+/* hmg_equilibrium for callers that cannot allocate device memory.  The paper has no
+ * counterpart; this entry point exists for hosts that own all device memory through
+ * their own pool, or that must not risk an allocation failure or the implicit device
+ * synchronization of cudaMalloc/cudaFree in the middle of a run.  It needs no context
+ * and calls no cudaMalloc, cudaFree or allocating library routine: its scratch (about
+ * 13 MB: the field, the packed spectrum, partial sums and the twiddle table of one
+ * N <= HMG_NOALLOC_MAX_N grid) is a set of static device arrays that every GPU which
+ * loads libhmg holds until the process exits.
+ * Same arithmetic as hmg_equilibrium with precision HMG_FP64: phase (N^3 bytes) and e
+ * (3 N^3 doubles) may be host or device pointers of the current device;
+ * eps_eq_out (1 double) and flux_mean_out (NULL or 3 doubles, <k e>) are host memory.
+ * Work runs on the current device's legacy default stream and the call returns when
+ * it has finished.  The first call on a device looks up the arrays' device addresses
+ * (cudaGetSymbolAddress) and caches them; make that first call before any stream
+ * capture.  All calls share the arrays, which keep the last call's contents (the
+ * sums are cleared at the start of every call): calls that overlap on the GPU, from
+ * several host threads or processes sharing a context, race with each other.
+ * Errors: HMG_INVALID_ARG for N > HMG_NOALLOC_MAX_N (or any argument hmg_equilibrium
+ * rejects), HMG_CUDA_ERROR if a CUDA call fails. */
+hmg_status hmg_equilibrium_noalloc(const uint8_t* phase, int N, double k_matrix,
+                                   double k_incl, double k_coat, const double* e,
+                                   double* eps_eq_out, double* flux_mean_out);
+
 /* ---- many RVEs: batched solves and the request loop ------------------------- */
 
 /* Solve `count` RVEs (possibly of different N) together: each batched sweep

@@ -29,7 +29,8 @@ STATUS_NAMES = {0: "OK", 1: "PENDING", -1: "INVALID_ARG", -2: "OUT_OF_MEMORY", -
 EXPORTS = ["hmg_version", "hmg_last_error", "hmg_create", "hmg_destroy", "hmg_voxelize", "hmg_solve",
            "hmg_solve_fields", "hmg_em_iterate", "hmg_equilibrium", "hmg_fft_forward", "hmg_fft_inverse",
            "hmg_solve_batch", "hmg_submit", "hmg_poll", "hmg_footprint", "hmg_trace_enable",
-           "hmg_trace_read"]
+           "hmg_trace_read", "hmg_equilibrium_noalloc"]
+HMG_NOALLOC_MAX_N = 64
 KERNEL_KINDS = ["x_forward", "y_forward", "z_green", "y_inverse", "x_inverse", "eq_x", "eq_z", "other"]
 
 
@@ -80,6 +81,7 @@ def lib() -> C.CDLL:
         L.hmg_solve_batch.argtypes = [vp, i, C.POINTER(vp), C.POINTER(i), dp, d, i, i, dp, C.POINTER(hmg_info)]
         L.hmg_submit.argtypes = [vp, vp, i, d, d, d, d, i, C.POINTER(C.c_uint64)]
         L.hmg_poll.argtypes = [vp, C.c_uint64, dp, C.POINTER(hmg_info)]
+        L.hmg_equilibrium_noalloc.argtypes = [vp, i, d, d, d, vp, dp, dp]
         L.hmg_trace_enable.argtypes = [vp, i]
         L.hmg_trace_read.argtypes = [vp, i, dp, C.POINTER(C.c_longlong), dp]
         L.hmg_footprint.argtypes = [i, i]
@@ -176,6 +178,15 @@ def hmg_equilibrium(ctx: int, phase, N: int, k, precision: int, e):
     flux = np.zeros(3)
     _check(lib().hmg_equilibrium(ctx, _ptr(phase), N, k[0], k[1], k[2], precision, _ptr(e), _dbuf(eps),
                                  _dbuf(flux)))
+    return float(eps[0]), flux
+
+
+def hmg_equilibrium_noalloc(phase, N: int, k, e):
+    """hmg_equilibrium (FP64) with static scratch, for callers that cannot allocate
+    device memory; N <= HMG_NOALLOC_MAX_N; runs on the current device."""
+    eps = np.zeros(1)
+    flux = np.zeros(3)
+    _check(lib().hmg_equilibrium_noalloc(_ptr(phase), N, k[0], k[1], k[2], _ptr(e), _dbuf(eps), _dbuf(flux)))
     return float(eps[0]), flux
 
 
