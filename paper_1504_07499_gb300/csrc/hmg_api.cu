@@ -337,7 +337,7 @@ void Solver::sweep(unsigned mask, R* field, void* spec, int zmode, int ximode, c
     if (ximode == XI_DIFF) xb = f * F + f * F + 2 * f * 4;      // spectrum, old field, d and r out
     HMG_TRACED(HMG_K_X_INVERSE, xb,
                launch_x_inverse<R>(g, ximode, mask, spec, field, r32in, d32, r32out, s->partial, st));
-    HMG_TRACED(HMG_K_OTHER, 0.0, launch_reduce(s->partial, g.nslots, x_ctas(g), 1, s->red, st));
+    HMG_TRACED(HMG_K_OTHER, 0.0, launch_reduce(s->partial, g.nslots, x_ctas_for<R>(g), 1, s->red, st));
 }
 
 template <typename R>
@@ -346,10 +346,10 @@ void Solver::equilibrium(unsigned mask, const R* field, void* spec) {
     const double F = sizeof(R);
     HMG_TRACED(HMG_K_EQ_X, f * 2 * F + (double)g.N3,
                launch_x_forward<R>(g, XF_FLUX, mask, field, spec, s->partial, st));
-    HMG_TRACED(HMG_K_OTHER, 0.0, launch_reduce(s->partial, g.nslots, x_ctas(g), 3, s->red + 16, st));
+    HMG_TRACED(HMG_K_OTHER, 0.0, launch_reduce(s->partial, g.nslots, x_ctas_for<R>(g), 3, s->red + 16, st));
     HMG_TRACED(HMG_K_Y_FORWARD, f * 2 * F, launch_y_pass<R>(g, true, mask, spec, st));
     HMG_TRACED(HMG_K_EQ_Z, f * F, launch_z_pass<R>(g, Z_EQ, mask, spec, s->partial2, st));
-    HMG_TRACED(HMG_K_OTHER, 0.0, launch_reduce(s->partial2, g.nslots, z_ctas(g), 1, s->red + 32, st));
+    HMG_TRACED(HMG_K_OTHER, 0.0, launch_reduce(s->partial2, g.nslots, z_ctas_for<R>(g), 1, s->red + 32, st));
 }
 
 bool Solver::fetch(double* h, int off, int count) {

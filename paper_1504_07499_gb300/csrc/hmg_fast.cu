@@ -1,0 +1,599 @@
+// Register-resident FFT passes (FP32) for the common grid sizes.
+//
+// A 1D transform of length L = E * TP runs as two register stages (the four-step
+// factorization; n = TP n1 + n2, k = k1 + E k2):
+//   stage 1: thread n2 holds x[TP n1 + n2] (n1 < E) straight from HBM, computes the
+//            length-E DFT over n1 in registers and multiplies by w_L^(n2 k1);
+//   exchange through shared memory (one write, one read);
+//   stage 2: thread t holds, for its E/TP values of k1, all TP values of n2 and
+//            computes length-TP DFTs, giving X[k1 + E k2] in registers.
+// X(k1 + E k2) = sum_n1 w_E^(n1 k1) w_L^(n2 k1) sum_n2 ... is the textbook split of the
+// DFT sum; the inverse runs the same stages with conjugate factors, or in reverse order
+// when it starts from stage-2 registers (z pass: forward, Green operator in registers,
+// inverse back to the natural layout without an extra exchange).
+// Loads and stores go between HBM and registers with the pencil index fastest across
+// threads, so every warp access is a run of contiguous bytes.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "hmg_fft.cuh"
+#include "hmg_green.cuh"
+#include "hmg_internal.h"
+
+namespace hmg {
+namespace fast {
+
+// cos(2 pi i / 96) for i = 0..24 (first quadrant), from the power series.
+__host__ __device__ constexpr double cos96_q(int i) {
+    return i == 0 ? 1.0 : i == 1 ? 0.9978589232386035 : i == 2 ? 0.9914448613738104 : i == 3 ? 0.9807852804032304
+         : i == 4 ? 0.9659258262890683 : i == 5 ? 0.9469301294951057 : i == 6 ? 0.9238795325112867
+         : i == 7 ? 0.8968727415326883 : i == 8 ? 0.8660254037844386 : i == 9 ? 0.8314696123025452
+         : i == 10 ? 0.7933533402912352 : i == 11 ? 0.7518398074789774 : i == 12 ? 0.7071067811865476
+         : i == 13 ? 0.6593458151000688 : i == 14 ? 0.6087614290087207 : i == 15 ? 0.5555702330196022
+         : i == 16 ? 0.5 : i == 17 ? 0.4422886902190013 : i == 18 ? 0.3826834323650898
+         : i == 19 ? 0.3214394653031616 : i == 20 ? 0.25881904510252074 : i == 21 ? 0.19509032201612828
+         : i == 22 ? 0.1305261922200516 : i == 23 ? 0.06540312923014306 : 0.0;
+}
+__host__ __device__ constexpr double cos96(int i) {
+    return (i = ((i % 96) + 96) % 96, i <= 24 ? cos96_q(i) : i <= 48 ? -cos96_q(48 - i)
+                                                    : i <= 72 ? -cos96_q(i - 48) : cos96_q(96 - i));
+}
+// w_E^m = exp(-2 pi i m / E) (forward) or its conjugate, for E dividing 96.
+template <int E, bool FWD>
+__device__ __forceinline__ float2 wE(int m) {
+    const float c = (float)cos96(m * (96 / E));
+    const float s = (float)cos96(m * (96 / E) - 24);   // sin(2 pi i / 96)
+    return FWD ? make_float2(c, -s) : make_float2(c, s);
+}
+
+// Length-E DFT in registers, natural order in and out.
+template <int E, bool FWD>
+struct RegDFT {
+    static constexpr int A = (E % 4 == 0) ? 4 : ((E % 2 == 0) ? 2 : 3);
+    static constexpr int B = E / A;
+    __device__ __forceinline__ static void run(float2* v) {
+        float2 s[A][B];
+#pragma unroll
+        for (int a = 0; a < A; ++a)
+#pragma unroll
+            for (int j = 0; j < B; ++j) s[a][j] = v[A * j + a];
+#pragma unroll
+        for (int a = 0; a < A; ++a) RegDFT<B, FWD>::run(s[a]);
+#pragma unroll
+        for (int a = 1; a < A; ++a)
+#pragma unroll
+            for (int k = 1; k < B; ++k) s[a][k] = cmul(s[a][k], wE<E, FWD>(a * k));
+#pragma unroll
+        for (int k = 0; k < B; ++k) {
+            float2 t[A];
+#pragma unroll
+            for (int a = 0; a < A; ++a) t[a] = s[a][k];
+            RegDFT<A, FWD>::run(t);
+#pragma unroll
+            for (int q = 0; q < A; ++q) v[k + B * q] = t[q];
+        }
+    }
+};
+template <bool FWD> struct RegDFT<1, FWD> { __device__ __forceinline__ static void run(float2*) {} };
+template <bool FWD> struct RegDFT<2, FWD> { __device__ __forceinline__ static void run(float2* v) { bfly2<FWD>(v); } };
+template <bool FWD> struct RegDFT<3, FWD> { __device__ __forceinline__ static void run(float2* v) { bfly3<FWD>(v); } };
+template <bool FWD> struct RegDFT<4, FWD> { __device__ __forceinline__ static void run(float2* v) { bfly4<FWD>(v); } };
+template <bool FWD> struct RegDFT<8, FWD> { __device__ __forceinline__ static void run(float2* v) { bfly8<FWD>(v); } };
+
+// Split of a length into E * TP with TP^2 dividing L (so each stage-2 thread owns
+// E/TP whole length-TP transforms).
+template <int L> struct Split;
+template <> struct Split<16> { static constexpr int TP = 4, E = 4; };
+template <> struct Split<32> { static constexpr int TP = 4, E = 8; };
+template <> struct Split<48> { static constexpr int TP = 4, E = 12; };
+template <> struct Split<64> { static constexpr int TP = 8, E = 8; };
+template <> struct Split<96> { static constexpr int TP = 4, E = 24; };
+template <> struct Split<128> { static constexpr int TP = 8, E = 16; };
+template <> struct Split<192> { static constexpr int TP = 8, E = 24; };
+template <> struct Split<256> { static constexpr int TP = 16, E = 16; };
+
+// Shared-memory slot of (k1, n2) of one pencil: k1-major with one pad row per group of
+// E/TP k1 values, so that stage-2 readers of different groups fall on different banks.
+template <int L>
+__device__ __forceinline__ int xslot(int k1, int n2) {
+    constexpr int TP = Split<L>::TP, KPT = Split<L>::E / TP;
+    return k1 * TP + n2 + (k1 / KPT);
+}
+template <int L> constexpr int xslots() { return L + Split<L>::E / (Split<L>::E / Split<L>::TP); }
+
+// stage 1 (+ twiddle) and the write half of the exchange
+template <int L, bool FWD>
+__device__ __forceinline__ void stage1_write(float2* v, int n2, const float2* __restrict__ twL, float2* sh, int pstride) {
+    constexpr int E = Split<L>::E;
+    RegDFT<E, FWD>::run(v);
+#pragma unroll
+    for (int k1 = 1; k1 < E; ++k1) {
+        const float2 w = __ldg(&twL[(n2 * k1) % L]);
+        v[k1] = FWD ? cmul(v[k1], w) : cmulc(v[k1], w);
+    }
+#pragma unroll
+    for (int k1 = 0; k1 < E; ++k1) sh[xslot<L>(k1, n2) * pstride] = v[k1];
+}
+
+// read half of the exchange and stage 2: v[i * TP + k2] = X[(t KPT + i) + E k2]
+template <int L, bool FWD>
+__device__ __forceinline__ void stage2_read(float2* v, int t, const float2* sh, int pstride) {
+    constexpr int E = Split<L>::E, TP = Split<L>::TP, KPT = E / TP;
+#pragma unroll
+    for (int i = 0; i < KPT; ++i) {
+        const int k1 = t * KPT + i;
+#pragma unroll
+        for (int n2 = 0; n2 < TP; ++n2) v[i * TP + n2] = sh[xslot<L>(k1, n2) * pstride];
+        RegDFT<TP, FWD>::run(v + i * TP);
+    }
+}
+
+// Reverse of stage 2 for an inverse transform that starts from the stage-2 layout:
+// inverse length-TP DFTs, conjugate twiddles w_L^-(n2 k1), write for the exchange.
+template <int L>
+__device__ __forceinline__ void rstage2_write(float2* v, int t, const float2* __restrict__ twL, float2* sh, int pstride) {
+    constexpr int E = Split<L>::E, TP = Split<L>::TP, KPT = E / TP;
+#pragma unroll
+    for (int i = 0; i < KPT; ++i) {
+        const int k1 = t * KPT + i;
+        RegDFT<TP, false>::run(v + i * TP);
+#pragma unroll
+        for (int n2 = 0; n2 < TP; ++n2) {
+            float2 x = v[i * TP + n2];
+            if (n2 > 0 && k1 > 0) x = cmulc(x, __ldg(&twL[(n2 * k1) % L]));
+            sh[xslot<L>(k1, n2) * pstride] = x;
+        }
+    }
+}
+
+// read half of the reverse exchange and the inverse length-E DFT: v[n1] = x[TP n1 + n2]
+template <int L>
+__device__ __forceinline__ void rstage1_read(float2* v, int n2, const float2* sh, int pstride) {
+    constexpr int E = Split<L>::E;
+#pragma unroll
+    for (int k1 = 0; k1 < E; ++k1) v[k1] = sh[xslot<L>(k1, n2) * pstride];
+    RegDFT<E, false>::run(v);
+}
+
+__device__ __forceinline__ float sel3f(int ph, float a, float b, float c) { return ph == 0 ? a : (ph == 1 ? b : c); }
+
+__device__ double block_sum_d(double v, double* sh) {
+    sh[threadIdx.x] = v;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+        __syncthreads();
+    }
+    double r = sh[0];
+    __syncthreads();
+    return r;
+}
+
+// ---------------------------------------------------------------------------
+// y pass: P consecutive kx columns of one (component, z) plane; threads (p, t)
+// ---------------------------------------------------------------------------
+
+template <int L, int P, bool FWD>
+__global__ void __launch_bounds__(P * Split<L>::TP)
+k_fy(GridDesc g, unsigned mask, float2* __restrict__ spec) {
+    constexpr int E = Split<L>::E, TP = Split<L>::TP;
+    const int slot = blockIdx.y;
+    if (!((mask >> slot) & 1u)) return;
+    extern __shared__ __align__(16) float2 sh[];   // xslots<L>() * P
+    const int M = g.M;
+    const int p = threadIdx.x % P, t = threadIdx.x / P;
+    const int nkb = M / P;
+    const int kb = blockIdx.x % nkb;
+    const long long cz = blockIdx.x / nkb;
+    float2* base = spec + (long long)slot * 3 * g.NNM + cz * (long long)L * M + kb * P + p;
+    float2 v[E];
+#pragma unroll
+    for (int n1 = 0; n1 < E; ++n1) v[n1] = base[(long long)(TP * n1 + t) * M];
+    const float2* twL = g.tw32 + g.pN.tw_off;
+    stage1_write<L, FWD>(v, t, twL, sh + p, P);
+    __syncthreads();
+    stage2_read<L, FWD>(v, t, sh + p, P);
+    constexpr int KPT = E / TP;
+#pragma unroll
+    for (int i = 0; i < KPT; ++i)
+#pragma unroll
+        for (int k2 = 0; k2 < TP; ++k2) base[(long long)(t * KPT + i + E * k2) * M] = v[i * TP + k2];
+}
+
+// ---------------------------------------------------------------------------
+// z pass: P consecutive kx columns at one ky, three components per thread
+// ---------------------------------------------------------------------------
+
+template <int L, int P, int MODE>
+__global__ void __launch_bounds__(P * Split<L>::TP)
+k_fz(GridDesc g, unsigned mask, float2* __restrict__ spec, double* __restrict__ partial) {
+    constexpr int E = Split<L>::E, TP = Split<L>::TP, KPT = E / TP;
+    constexpr int NS = xslots<L>() * P;
+    const int slot = blockIdx.y;
+    if (!((mask >> slot) & 1u)) return;
+    extern __shared__ __align__(16) float2 sh[];   // 3 * NS
+    __shared__ double red[P * TP];
+    const int N = g.N, M = g.M;
+    const int p = threadIdx.x % P, t = threadIdx.x / P;
+    const int nkb = M / P;
+    const int kb = blockIdx.x % nkb;
+    const int ky = blockIdx.x / nkb;
+    const int kx = kb * P + p;
+    float2* base = spec + (long long)slot * 3 * g.NNM + (long long)ky * M + kb * P + p;
+    const long long rowz = (long long)N * M;     // stride between z rows
+    const float2* twL = g.tw32 + g.pN.tw_off;
+    float2 v[3][E];
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int n1 = 0; n1 < E; ++n1) v[c][n1] = base[c * g.NNM + (long long)(TP * n1 + t) * rowz];
+
+    if (MODE == Z_INV) {
+        // plain inverse transform of each component (natural order in and out)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) stage1_write<L, false>(v[c], t, twL, sh + c * NS + p, P);
+        __syncthreads();
+#pragma unroll
+        for (int c = 0; c < 3; ++c) stage2_read<L, false>(v[c], t, sh + c * NS + p, P);
+    } else {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) stage1_write<L, true>(v[c], t, twL, sh + c * NS + p, P);
+        __syncthreads();
+#pragma unroll
+        for (int c = 0; c < 3; ++c) stage2_read<L, true>(v[c], t, sh + c * NS + p, P);
+    }
+    if (MODE == Z_FWD || MODE == Z_INV) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int i = 0; i < KPT; ++i)
+#pragma unroll
+                for (int k2 = 0; k2 < TP; ++k2)
+                    base[c * g.NNM + (long long)(t * KPT + i + E * k2) * rowz] = v[c][i * TP + k2];
+        return;
+    }
+    if (MODE == Z_EQ) {
+        double acc = 0.0;
+#pragma unroll
+        for (int i = 0; i < KPT; ++i)
+#pragma unroll
+            for (int k2 = 0; k2 < TP; ++k2)
+                acc += eq_mode(kx, ky, t * KPT + i + E * k2, N, v[0][i * TP + k2], v[1][i * TP + k2], v[2][i * TP + k2]);
+        const double twopi_n = 6.283185307179586476925 / (double)N;
+        const double s = block_sum_d(acc, red) * twopi_n * twopi_n / ((double)g.N3 * (double)g.N3);
+        if (threadIdx.x == 0) partial[(long long)slot * gridDim.x + blockIdx.x] = s;
+        return;
+    }
+    // Green operator on the registers, then the inverse back to natural order
+    const float scale = (float)(1.0 / (double)g.N3);
+    const float twok0E[3] = {(float)(2.0 * g.k0 * g.E[slot][0]), (float)(2.0 * g.k0 * g.E[slot][1]),
+                             (float)(2.0 * g.k0 * g.E[slot][2])};
+#pragma unroll
+    for (int i = 0; i < KPT; ++i)
+#pragma unroll
+        for (int k2 = 0; k2 < TP; ++k2)
+            green_mode<float>(kx, ky, t * KPT + i + E * k2, N, scale, MODE == Z_ITER, twok0E, v[0][i * TP + k2],
+                              v[1][i * TP + k2], v[2][i * TP + k2]);
+    __syncthreads();   // every thread has read the forward exchange
+#pragma unroll
+    for (int c = 0; c < 3; ++c) rstage2_write<L>(v[c], t, twL, sh + c * NS + p, P);
+    __syncthreads();
+#pragma unroll
+    for (int c = 0; c < 3; ++c) rstage1_read<L>(v[c], t, sh + c * NS + p, P);
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int n1 = 0; n1 < E; ++n1) base[c * g.NNM + (long long)(TP * n1 + t) * rowz] = v[c][n1];
+}
+
+// ---------------------------------------------------------------------------
+// x passes: R rows per CTA, threads (t, r) with t fastest along the row
+// ---------------------------------------------------------------------------
+
+template <int M> constexpr int row_stride() {
+    // slots per row, padded to an odd multiple of 8 complex values (64 B) so that
+    // rows of a warp start on alternating bank halves
+    return ((xslots<M>() + 15) / 16) * 16 + 8;
+}
+
+template <int M, int RW, int MODE>
+__global__ void __launch_bounds__(RW * Split<M>::TP)
+k_fx_forward(GridDesc g, unsigned mask, const float* __restrict__ tau, float2* __restrict__ spec,
+             double* __restrict__ partial) {
+    constexpr int E = Split<M>::E, TP = Split<M>::TP, KPT = E / TP, RS = row_stride<M>();
+    const int slot = blockIdx.y;
+    if (!((mask >> slot) & 1u)) return;
+    extern __shared__ __align__(16) float2 sh[];   // RW * RS
+    __shared__ double red[RW * TP];
+    const int N = g.N;
+    const int t = threadIdx.x % TP, r = threadIdx.x / TP;
+    const long long row = (long long)blockIdx.x * RW + r;            // c*NN + z*N + y
+    const float2* src = reinterpret_cast<const float2*>(tau + (long long)slot * 3 * g.N3 + row * N);
+    const uchar2* ph = reinterpret_cast<const uchar2*>(g.phase + (row % g.NN) * N);
+    float2 v[E];
+#pragma unroll
+    for (int n1 = 0; n1 < E; ++n1) v[n1] = src[TP * n1 + t];
+    float acc = 0.f;
+    if (MODE != XF_PLAIN) {
+        const float c0 = (float)(MODE == XF_POLARIZE ? g.Y[0] : g.W[0]);
+        const float c1 = (float)(MODE == XF_POLARIZE ? g.Y[1] : g.W[1]);
+        const float c2 = (float)(MODE == XF_POLARIZE ? g.Y[2] : g.W[2]);
+#pragma unroll
+        for (int n1 = 0; n1 < E; ++n1) {
+            const uchar2 q = ph[TP * n1 + t];
+            v[n1].x *= sel3f(q.x, c0, c1, c2);
+            v[n1].y *= sel3f(q.y, c0, c1, c2);
+            if (MODE == XF_FLUX) acc += v[n1].x + v[n1].y;
+        }
+    }
+    const float2* twM = g.tw32 + g.pM.tw_off;
+    float2* rs = sh + r * RS;
+    stage1_write<M, true>(v, t, twM, rs, 1);
+    __syncthreads();
+    stage2_read<M, true>(v, t, rs, 1);
+    __syncthreads();
+    // natural order into shared memory for the real split
+#pragma unroll
+    for (int i = 0; i < KPT; ++i)
+#pragma unroll
+        for (int k2 = 0; k2 < TP; ++k2) rs[t * KPT + i + E * k2] = v[i * TP + k2];
+    if (MODE == XF_FLUX) {
+        const double s = block_sum_d((double)acc, red);
+        if (threadIdx.x == 0) partial[(long long)slot * gridDim.x + blockIdx.x] = s;
+    } else {
+        __syncthreads();
+    }
+    const float2* twN = g.tw32 + g.pN.tw_off;
+    float2* dst = spec + (long long)slot * 3 * g.NNM + row * M;
+#pragma unroll
+    for (int j = 0; j < E; ++j) {
+        const int k = t + TP * j;
+        const float2 z = rs[k];
+        float2 out;
+        if (k == 0) {
+            out = make_float2(z.x + z.y, z.x - z.y);
+        } else {
+            const float2 zm = rs[M - k];
+            const float2 e = make_float2(0.5f * (z.x + zm.x), 0.5f * (z.y - zm.y));
+            const float2 o = make_float2(0.5f * (z.y + zm.y), -0.5f * (z.x - zm.x));
+            out = cadd(e, cmul(o, __ldg(&twN[k])));
+        }
+        dst[k] = out;
+    }
+}
+
+template <int M, int RW, int MODE>
+__global__ void __launch_bounds__(RW * Split<M>::TP)
+k_fx_inverse(GridDesc g, unsigned mask, const float2* __restrict__ spec, float* __restrict__ tau,
+             const float* __restrict__ r32, double* __restrict__ partial) {
+    constexpr int E = Split<M>::E, TP = Split<M>::TP, KPT = E / TP, RS = row_stride<M>();
+    const int slot = blockIdx.y;
+    if (!((mask >> slot) & 1u)) return;
+    extern __shared__ __align__(16) float2 sh[];   // RW * RS
+    __shared__ double red[RW * TP];
+    const int N = g.N;
+    const int t = threadIdx.x % TP, r = threadIdx.x / TP;
+    const long long row = (long long)blockIdx.x * RW + r;
+    const long long fbase = (long long)slot * 3 * g.N3 + row * N;
+    float2* out = reinterpret_cast<float2*>(tau + fbase);
+    // prefetch the old field (and r) for the output step: in flight during the FFT
+    float2 old[E], radd[E];
+    if (MODE == XI_INPLACE_RES || MODE == XI_ADD_R_RES) {
+#pragma unroll
+        for (int j = 0; j < E; ++j) old[j] = out[t + TP * j];
+    }
+    if (MODE == XI_ADD_R_RES) {
+        const float2* rr = reinterpret_cast<const float2*>(r32 + fbase);
+#pragma unroll
+        for (int j = 0; j < E; ++j) radd[j] = rr[t + TP * j];
+    }
+    const float2* src = spec + (long long)slot * 3 * g.NNM + row * M;
+    float2* rs = sh + r * RS;
+#pragma unroll
+    for (int j = 0; j < E; ++j) rs[t + TP * j] = src[t + TP * j];
+    __syncthreads();
+    // complex-to-real merge into the stage-1 layout
+    const float2* twN = g.tw32 + g.pN.tw_off;
+    float2 v[E];
+#pragma unroll
+    for (int n1 = 0; n1 < E; ++n1) {
+        const int k = TP * n1 + t;
+        float2 xk, xm;
+        if (k == 0) {
+            const float2 q = rs[0];
+            xk = make_float2(q.x, 0.f);
+            xm = make_float2(q.y, 0.f);
+        } else {
+            xk = rs[k];
+            xm = rs[M - k];
+        }
+        const float2 s = make_float2(xk.x + xm.x, xk.y - xm.y);
+        const float2 d = make_float2(xk.x - xm.x, xk.y + xm.y);
+        const float2 dw = cmulc(d, __ldg(&twN[k]));
+        v[n1] = make_float2(s.x - dw.y, s.y + dw.x);
+    }
+    __syncthreads();
+    const float2* twM = g.tw32 + g.pM.tw_off;
+    stage1_write<M, false>(v, t, twM, rs, 1);
+    __syncthreads();
+    stage2_read<M, false>(v, t, rs, 1);
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < KPT; ++i)
+#pragma unroll
+        for (int k2 = 0; k2 < TP; ++k2) rs[t * KPT + i + E * k2] = v[i * TP + k2];
+    __syncthreads();
+    float acc = 0.f;
+#pragma unroll
+    for (int j = 0; j < E; ++j) {
+        float2 x = rs[t + TP * j];
+        if (MODE == XI_ADD_R_RES) {
+            x.x += radd[j].x;
+            x.y += radd[j].y;
+        }
+        if (MODE == XI_INPLACE_RES || MODE == XI_ADD_R_RES) {
+            const float da = x.x - old[j].x, db = x.y - old[j].y;
+            acc += da * da + db * db;
+        }
+        out[t + TP * j] = x;
+    }
+    if (MODE == XI_INPLACE_RES || MODE == XI_ADD_R_RES) {
+        const double s = block_sum_d((double)acc, red);
+        if (threadIdx.x == 0) partial[(long long)slot * gridDim.x + blockIdx.x] = s;
+    }
+}
+
+}  // namespace fast
+
+// ---------------------------------------------------------------------------
+// dispatch: a fast kernel exists for FP32 and the lengths with a Split above
+// ---------------------------------------------------------------------------
+
+namespace {
+// Launch with `bytes` of dynamic shared memory.  Static plus dynamic shared memory
+// above 48 KB needs the opt-in, so it is requested whenever the two could exceed it.
+template <typename K, typename... Args>
+void launch_dyn(K kern, dim3 grid, int threads, size_t bytes, cudaStream_t st, Args... args) {
+    if (bytes > 32 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    kern<<<grid, threads, bytes, st>>>(args...);
+}
+template <int L> constexpr int fy_cols() { return 256 / fast::Split<L>::TP; }
+template <int L> constexpr int fz_cols() { return 128 / fast::Split<L>::TP; }
+template <int M> constexpr int fx_rows() { return 256 / fast::Split<M>::TP; }
+}  // namespace
+
+#define HMG_FAST_LEN(L, X) \
+    case L: X(L); return true;
+
+bool fast_y(const GridDesc& g, bool fwd, unsigned mask, void* spec, cudaStream_t st) {
+    float2* sp = reinterpret_cast<float2*>(spec);
+#define FY(L)                                                                                     \
+    {                                                                                             \
+        constexpr int P = fy_cols<L>();                                                           \
+        if (g.M % P) return false;                                                                \
+        dim3 grid(3 * g.N * (g.M / P), g.nslots);                                                 \
+        const size_t sm = sizeof(float2) * fast::xslots<L>() * P;                                 \
+        if (fwd) launch_dyn(fast::k_fy<L, P, true>, grid, P * fast::Split<L>::TP, sm, st, g, mask, sp);  \
+        else launch_dyn(fast::k_fy<L, P, false>, grid, P * fast::Split<L>::TP, sm, st, g, mask, sp);     \
+    }
+    switch (g.N) {
+        HMG_FAST_LEN(64, FY)
+        HMG_FAST_LEN(96, FY)
+        HMG_FAST_LEN(128, FY)
+        HMG_FAST_LEN(192, FY)
+        HMG_FAST_LEN(256, FY)
+        default: return false;
+    }
+#undef FY
+}
+
+int fast_z_ctas(const GridDesc& g) {
+    int P = 0;
+    switch (g.N) {
+        case 64: P = fz_cols<64>(); break;
+        case 96: P = fz_cols<96>(); break;
+        case 128: P = fz_cols<128>(); break;
+        case 192: P = fz_cols<192>(); break;
+        case 256: P = fz_cols<256>(); break;
+        default: return 0;
+    }
+    if (g.M % P) return 0;
+    return g.N * (g.M / P);
+}
+
+bool fast_z(const GridDesc& g, int mode, unsigned mask, void* spec, double* partial, cudaStream_t st) {
+    float2* sp = reinterpret_cast<float2*>(spec);
+#define FZ(L)                                                                                          \
+    {                                                                                                  \
+        constexpr int P = fz_cols<L>();                                                                \
+        constexpr int T = P * fast::Split<L>::TP;                                                      \
+        if (g.M % P) return false;                                                                     \
+        dim3 grid(g.N * (g.M / P), g.nslots);                                                          \
+        const size_t sm = sizeof(float2) * 3 * fast::xslots<L>() * P;                                  \
+        switch (mode) {                                                                                \
+            case Z_FWD: launch_dyn(fast::k_fz<L, P, Z_FWD>, grid, T, sm, st, g, mask, sp, partial); break;   \
+            case Z_INV: launch_dyn(fast::k_fz<L, P, Z_INV>, grid, T, sm, st, g, mask, sp, partial); break;   \
+            case Z_ITER: launch_dyn(fast::k_fz<L, P, Z_ITER>, grid, T, sm, st, g, mask, sp, partial); break; \
+            case Z_ITER_NOB: launch_dyn(fast::k_fz<L, P, Z_ITER_NOB>, grid, T, sm, st, g, mask, sp, partial); break; \
+            default: launch_dyn(fast::k_fz<L, P, Z_EQ>, grid, T, sm, st, g, mask, sp, partial); break;       \
+        }                                                                                              \
+    }
+    switch (g.N) {
+        HMG_FAST_LEN(64, FZ)
+        HMG_FAST_LEN(96, FZ)
+        HMG_FAST_LEN(128, FZ)
+        HMG_FAST_LEN(192, FZ)
+        HMG_FAST_LEN(256, FZ)
+        default: return false;
+    }
+#undef FZ
+}
+
+int fast_x_ctas(const GridDesc& g) {
+    int RW = 0;
+    switch (g.M) {
+        case 32: RW = fx_rows<32>(); break;
+        case 48: RW = fx_rows<48>(); break;
+        case 64: RW = fx_rows<64>(); break;
+        case 96: RW = fx_rows<96>(); break;
+        case 128: RW = fx_rows<128>(); break;
+        default: return 0;
+    }
+    if ((3 * g.NN) % RW || g.NN % RW) return 0;
+    return (int)(3 * g.NN / RW);
+}
+
+bool fast_x_forward(const GridDesc& g, int mode, unsigned mask, const float* tau, void* spec, double* partial,
+                    cudaStream_t st) {
+    float2* sp = reinterpret_cast<float2*>(spec);
+    if (!fast_x_ctas(g)) return false;
+#define FXF(M)                                                                                                 \
+    {                                                                                                          \
+        constexpr int RW = fx_rows<M>();                                                                       \
+        constexpr int T = RW * fast::Split<M>::TP;                                                             \
+        dim3 grid(fast_x_ctas(g), g.nslots);                                                                   \
+        const size_t sm = sizeof(float2) * RW * fast::row_stride<M>();                                         \
+        if (mode == XF_PLAIN) launch_dyn(fast::k_fx_forward<M, RW, XF_PLAIN>, grid, T, sm, st, g, mask, tau, sp, partial); \
+        else if (mode == XF_POLARIZE) launch_dyn(fast::k_fx_forward<M, RW, XF_POLARIZE>, grid, T, sm, st, g, mask, tau, sp, partial); \
+        else launch_dyn(fast::k_fx_forward<M, RW, XF_FLUX>, grid, T, sm, st, g, mask, tau, sp, partial);        \
+    }
+    switch (g.M) {
+        HMG_FAST_LEN(32, FXF)
+        HMG_FAST_LEN(48, FXF)
+        HMG_FAST_LEN(64, FXF)
+        HMG_FAST_LEN(96, FXF)
+        HMG_FAST_LEN(128, FXF)
+        default: return false;
+    }
+#undef FXF
+}
+
+bool fast_x_inverse(const GridDesc& g, int mode, unsigned mask, const void* spec, float* tau, const float* r32,
+                    double* partial, cudaStream_t st) {
+    const float2* sp = reinterpret_cast<const float2*>(spec);
+    if (!fast_x_ctas(g)) return false;
+    if (mode != XI_PLAIN && mode != XI_INPLACE && mode != XI_INPLACE_RES && mode != XI_ADD_R_RES) return false;
+#define FXI(M)                                                                                                         \
+    {                                                                                                                  \
+        constexpr int RW = fx_rows<M>();                                                                               \
+        constexpr int T = RW * fast::Split<M>::TP;                                                                     \
+        dim3 grid(fast_x_ctas(g), g.nslots);                                                                           \
+        const size_t sm = sizeof(float2) * RW * fast::row_stride<M>();                                                 \
+        if (mode == XI_INPLACE_RES) launch_dyn(fast::k_fx_inverse<M, RW, XI_INPLACE_RES>, grid, T, sm, st, g, mask, sp, tau, r32, partial); \
+        else if (mode == XI_ADD_R_RES) launch_dyn(fast::k_fx_inverse<M, RW, XI_ADD_R_RES>, grid, T, sm, st, g, mask, sp, tau, r32, partial); \
+        else launch_dyn(fast::k_fx_inverse<M, RW, XI_INPLACE>, grid, T, sm, st, g, mask, sp, tau, r32, partial);        \
+    }
+    switch (g.M) {
+        HMG_FAST_LEN(32, FXI)
+        HMG_FAST_LEN(48, FXI)
+        HMG_FAST_LEN(64, FXI)
+        HMG_FAST_LEN(96, FXI)
+        HMG_FAST_LEN(128, FXI)
+        default: return false;
+    }
+#undef FXI
+}
+
+#undef HMG_FAST_LEN
+
+}  // namespace hmg

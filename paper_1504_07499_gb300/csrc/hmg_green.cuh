@@ -1,0 +1,106 @@
+// The Green operator of §3 applied per Fourier mode, and the per-mode term of the
+// step-1 equilibrium norm, on the packed half spectrum (see hmg_kernels.cu for the
+// layout).  Gamma0 = -P/k0 with P = xi xi^T / |xi|^2, so the tau-form sweep needs
+// (I - 2P) s; the Nyquist rule decides xi at Nyquist components.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "hmg_internal.h"
+
+namespace hmg {
+
+__device__ __forceinline__ int signed_mode(int k, int N) { return k <= N / 2 ? k : k - N; }
+
+// Direction m' of the projector at mode (kx >= 0, my, mz) (signed modes): Nyquist
+// components are dropped unless they are the only nonzero component.  Returns |m'|^2
+// (0 where P = 0: at DC and at modes made only of two or three Nyquist components).
+__device__ __forceinline__ int mode_dir(int kx, int my, int mz, int N, int* d) {
+    const int h = N / 2;
+    const int nonzero = (kx != 0) + (my != 0) + (mz != 0);
+    d[0] = (kx == h && nonzero > 1) ? 0 : kx;
+    d[1] = (my == h && nonzero > 1) ? 0 : my;
+    d[2] = (mz == h && nonzero > 1) ? 0 : mz;
+    return d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+}
+
+template <typename R>
+__device__ __forceinline__ void reflect_real(R* a, int kx, int my, int mz, int N) {
+    int d[3];
+    const int n2 = mode_dir(kx, my, mz, N, d);
+    if (n2 > 0) {
+        const R f = R(2.0) / R(n2);
+        const R dot = R(d[0]) * a[0] + R(d[1]) * a[1] + R(d[2]) * a[2];
+        a[0] -= f * R(d[0]) * dot;
+        a[1] -= f * R(d[1]) * dot;
+        a[2] -= f * R(d[2]) * dot;
+    }
+}
+
+// s <- scale (I - 2P) s at packed mode (kx, ky, kz); at the DC of the kx = 0 plane
+// add 2 k0 E (when add_b).  kx in [0, N/2), ky, kz in [0, N).
+template <typename R, typename T2>
+__device__ __forceinline__ void green_mode(int kx, int ky, int kz, int N, R scale, bool add_b, const R* twok0E,
+                                           T2& s0, T2& s1, T2& s2) {
+    const int my = signed_mode(ky, N), mz = signed_mode(kz, N);
+    const bool special = (kx == 0) && (ky == 0 || ky == N / 2) && (kz == 0 || kz == N / 2);
+    if (!special) {
+        int d[3];
+        const int n2 = mode_dir(kx, my, mz, N, d);   // > 0 at every non-special mode
+        const R f = R(2.0) / R(n2);
+        const R dx = R(d[0]) * s0.x + R(d[1]) * s1.x + R(d[2]) * s2.x;
+        const R dy = R(d[0]) * s0.y + R(d[1]) * s1.y + R(d[2]) * s2.y;
+        s0.x = scale * (s0.x - f * R(d[0]) * dx);
+        s0.y = scale * (s0.y - f * R(d[0]) * dy);
+        s1.x = scale * (s1.x - f * R(d[1]) * dx);
+        s1.y = scale * (s1.y - f * R(d[1]) * dy);
+        s2.x = scale * (s2.x - f * R(d[2]) * dx);
+        s2.y = scale * (s2.y - f * R(d[2]) * dy);
+    } else {
+        R a[3] = {s0.x, s1.x, s2.x};   // plane kx = 0
+        R b[3] = {s0.y, s1.y, s2.y};   // plane kx = N/2
+        reflect_real(a, 0, my, mz, N);
+        reflect_real(b, N / 2, my, mz, N);
+        for (int c = 0; c < 3; ++c) {
+            a[c] *= scale;
+            b[c] *= scale;
+        }
+        if (add_b && ky == 0 && kz == 0)
+            for (int c = 0; c < 3; ++c) a[c] += twok0E[c];
+        s0.x = a[0];
+        s0.y = b[0];
+        s1.x = a[1];
+        s1.y = b[1];
+        s2.x = a[2];
+        s2.y = b[2];
+    }
+}
+
+// Weighted |m' . s|^2 of packed mode (kx, ky, kz) for the equilibrium norm (integer
+// m'; the caller scales by (2 pi / N)^2 / N^6).  Modes 0 < kx < N/2 stand for kx and
+// N - kx (weight 2); the kx = 0 column holds the kx = 0 and kx = N/2 planes, whose
+// cross terms cancel over +-k except at the four self-conjugate modes, split here.
+template <typename T2>
+__device__ __forceinline__ double eq_mode(int kx, int ky, int kz, int N, const T2& s0, const T2& s1, const T2& s2) {
+    const int my = signed_mode(ky, N), mz = signed_mode(kz, N);
+    const bool special = (kx == 0) && (ky == 0 || ky == N / 2) && (kz == 0 || kz == N / 2);
+    int d[3];
+    if (!special) {
+        if (mode_dir(kx, my, mz, N, d) == 0) return 0.0;
+        const double dr = d[0] * (double)s0.x + d[1] * (double)s1.x + d[2] * (double)s2.x;
+        const double di = d[0] * (double)s0.y + d[1] * (double)s1.y + d[2] * (double)s2.y;
+        return (kx == 0 ? 1.0 : 2.0) * (dr * dr + di * di);
+    }
+    double acc = 0.0;
+    if (mode_dir(0, my, mz, N, d) > 0) {
+        const double dr = d[0] * (double)s0.x + d[1] * (double)s1.x + d[2] * (double)s2.x;
+        acc += dr * dr;
+    }
+    if (mode_dir(N / 2, my, mz, N, d) > 0) {
+        const double di = d[0] * (double)s0.y + d[1] * (double)s1.y + d[2] * (double)s2.y;
+        acc += di * di;
+    }
+    return acc;
+}
+
+}  // namespace hmg

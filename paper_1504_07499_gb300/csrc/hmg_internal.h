@@ -62,8 +62,23 @@ void launch_x_inverse(const GridDesc& g, int mode, unsigned mask, const void* sp
                       const float* r32, float* d32, float* r32_out, double* partial,
                       cudaStream_t st);
 
-int x_ctas(const GridDesc& g);   // CTAs per right-hand side of the x passes
-int z_ctas(const GridDesc& g);   // CTAs per right-hand side of the z pass
+int x_ctas(const GridDesc& g);   // CTAs per right-hand side of the generic x passes
+int z_ctas(const GridDesc& g);   // CTAs per right-hand side of the generic z pass
+// CTAs per right-hand side of the x / z passes that launch_* runs for precision R
+// (the register-resident FP32 kernels where one exists, else the generic ones)
+template <typename R> int x_ctas_for(const GridDesc& g);
+template <typename R> int z_ctas_for(const GridDesc& g);
+
+// Register-resident FP32 kernels (hmg_fast.cu); each returns false (launching
+// nothing) when no specialization covers the grid size.
+bool fast_y(const GridDesc& g, bool fwd, unsigned mask, void* spec, cudaStream_t st);
+bool fast_z(const GridDesc& g, int mode, unsigned mask, void* spec, double* partial, cudaStream_t st);
+bool fast_x_forward(const GridDesc& g, int mode, unsigned mask, const float* tau, void* spec, double* partial,
+                    cudaStream_t st);
+bool fast_x_inverse(const GridDesc& g, int mode, unsigned mask, const void* spec, float* tau, const float* r32,
+                    double* partial, cudaStream_t st);
+int fast_x_ctas(const GridDesc& g);
+int fast_z_ctas(const GridDesc& g);
 
 // Sum `count` partials of each of `nslots` rows in a fixed order: out[s] = sum_i p[s*count+i].
 // `groups` > 1 splits each row into that many equal consecutive groups (out[s*groups+g]).

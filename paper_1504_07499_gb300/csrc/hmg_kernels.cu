@@ -19,7 +19,10 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "hmg_fft.cuh"
+#include "hmg_green.cuh"
 #include "hmg_internal.h"
 
 namespace hmg {
@@ -45,8 +48,6 @@ __device__ double block_sum(double v, double* sh) {
     __syncthreads();
     return r;
 }
-
-__device__ __forceinline__ int signed_mode(int k, int N) { return k <= N / 2 ? k : k - N; }
 
 // ---------------------------------------------------------------------------
 // x forward: rows of N reals -> N/2 packed complex values
@@ -229,20 +230,6 @@ k_y_pass(GridDesc g, unsigned mask, typename Cplx<R>::T* __restrict__ spec) {
 // inverse.  Z_EQ: forward, then sum |xi . phi_hat|^2 / N^6 in FP64.
 // ---------------------------------------------------------------------------
 
-// Projector data of one (kx, ky, kz) mode: unnormalized direction m' (integers) with
-// the Nyquist rule applied.  Returns |m'|^2 (0 where P = 0).
-__device__ __forceinline__ int mode_dir(int kx, int my, int mz, int N, int* d) {
-    const int h = N / 2;
-    const int nyq_y = (my == h), nyq_z = (mz == h);
-    const int nx = (kx != 0), ny = (my != 0), nz = (mz != 0);
-    const int nonzero = nx + ny + nz;
-    const int nyqx = (kx == h);
-    d[0] = (nyqx && nonzero > 1) ? 0 : kx;
-    d[1] = (nyq_y && nonzero > 1) ? 0 : my;
-    d[2] = (nyq_z && nonzero > 1) ? 0 : mz;
-    return d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
-}
-
 template <typename R, int MODE>
 __global__ void __launch_bounds__(kThreads)
 k_z_pass(GridDesc g, unsigned mask, typename Cplx<R>::T* __restrict__ spec, double* __restrict__ partial) {
@@ -270,80 +257,23 @@ k_z_pass(GridDesc g, unsigned mask, typename Cplx<R>::T* __restrict__ spec, doub
     T2* other = (res == b0) ? b1 : b0;
 
     if (MODE == Z_ITER || MODE == Z_ITER_NOB || MODE == Z_EQ) {
-        const int my = signed_mode(ky, N);
         const R scale = R(1.0 / (double)g.N3);
+        const R twok0E[3] = {R(2.0 * g.k0 * g.E[slot][0]), R(2.0 * g.k0 * g.E[slot][1]),
+                             R(2.0 * g.k0 * g.E[slot][2])};
         double acc = 0.0;
         const double twopi_n = 6.283185307179586476925 / (double)N;
         for (int q = threadIdx.x; q < N * P; q += blockDim.x) {
             const int kz = q / P, p = q - kz * P;
             const int kx = kb * P + p;
-            const int mz = signed_mode(kz, N);
             T2* e = res + kz * P3 + p;
             T2 s0 = e[0], s1 = e[P], s2 = e[2 * P];
-            const bool special = (kx == 0) && (ky == 0 || ky == N / 2) && (kz == 0 || kz == N / 2);
             if (MODE == Z_EQ) {
-                if (!special) {
-                    int d[3];
-                    const int n2 = mode_dir(kx, my, mz, N, d);
-                    if (n2 > 0) {
-                        const double dr = d[0] * (double)s0.x + d[1] * (double)s1.x + d[2] * (double)s2.x;
-                        const double di = d[0] * (double)s0.y + d[1] * (double)s1.y + d[2] * (double)s2.y;
-                        acc += (kx == 0 ? 1.0 : 2.0) * (dr * dr + di * di);
-                    }
-                } else {
-                    // real part: plane kx = 0; imaginary part: plane kx = N/2
-                    int d[3];
-                    if (mode_dir(0, my, mz, N, d) > 0) {
-                        const double dr = d[0] * (double)s0.x + d[1] * (double)s1.x + d[2] * (double)s2.x;
-                        acc += dr * dr;
-                    }
-                    if (mode_dir(N / 2, my, mz, N, d) > 0) {
-                        const double di = d[0] * (double)s0.y + d[1] * (double)s1.y + d[2] * (double)s2.y;
-                        acc += di * di;
-                    }
-                }
+                acc += eq_mode(kx, ky, kz, N, s0, s1, s2);
             } else {
-                T2 o0, o1, o2;
-                if (!special) {
-                    int d[3];
-                    const int n2 = mode_dir(kx, my, mz, N, d);
-                    // (I - 2P) s with P = d d^T / |d|^2 (n2 > 0 for every non-special mode)
-                    const R f = R(2.0) / R(n2);
-                    const T2 dot = mk(R(d[0]) * s0.x + R(d[1]) * s1.x + R(d[2]) * s2.x,
-                                      R(d[0]) * s0.y + R(d[1]) * s1.y + R(d[2]) * s2.y);
-                    o0 = mk(scale * (s0.x - f * R(d[0]) * dot.x), scale * (s0.y - f * R(d[0]) * dot.y));
-                    o1 = mk(scale * (s1.x - f * R(d[1]) * dot.x), scale * (s1.y - f * R(d[1]) * dot.y));
-                    o2 = mk(scale * (s2.x - f * R(d[2]) * dot.x), scale * (s2.y - f * R(d[2]) * dot.y));
-                } else {
-                    R a[3] = {s0.x, s1.x, s2.x};   // plane kx = 0
-                    R b[3] = {s0.y, s1.y, s2.y};   // plane kx = N/2
-                    int d[3];
-                    int n2 = mode_dir(0, my, mz, N, d);
-                    if (n2 > 0) {
-                        const R f = R(2.0) / R(n2);
-                        const R dot = R(d[0]) * a[0] + R(d[1]) * a[1] + R(d[2]) * a[2];
-                        for (int c = 0; c < 3; ++c) a[c] -= f * R(d[c]) * dot;
-                    }
-                    n2 = mode_dir(N / 2, my, mz, N, d);
-                    if (n2 > 0) {
-                        const R f = R(2.0) / R(n2);
-                        const R dot = R(d[0]) * b[0] + R(d[1]) * b[1] + R(d[2]) * b[2];
-                        for (int c = 0; c < 3; ++c) b[c] -= f * R(d[c]) * dot;
-                    }
-                    for (int c = 0; c < 3; ++c) {
-                        a[c] *= scale;
-                        b[c] *= scale;
-                    }
-                    if (MODE == Z_ITER && ky == 0 && kz == 0) {
-                        for (int c = 0; c < 3; ++c) a[c] += R(2.0 * g.k0 * g.E[slot][c]);
-                    }
-                    o0 = mk(a[0], b[0]);
-                    o1 = mk(a[1], b[1]);
-                    o2 = mk(a[2], b[2]);
-                }
-                e[0] = o0;
-                e[P] = o1;
-                e[2 * P] = o2;
+                green_mode<R>(kx, ky, kz, N, scale, MODE == Z_ITER, twok0E, s0, s1, s2);
+                e[0] = s0;
+                e[P] = s1;
+                e[2 * P] = s2;
             }
         }
         if (MODE == Z_EQ) {
@@ -448,15 +378,30 @@ static int pointwise_blocks(long long n) {
 int x_ctas(const GridDesc& g) { return (int)(3 * g.NN / g.rows); }
 int z_ctas(const GridDesc& g) { return g.N * (g.M / g.Pz); }
 
+template <> int x_ctas_for<float>(const GridDesc& g) {
+    const int f = fast_x_ctas(g);
+    return f ? f : x_ctas(g);
+}
+template <> int x_ctas_for<double>(const GridDesc& g) { return x_ctas(g); }
+template <> int z_ctas_for<float>(const GridDesc& g) {
+    const int f = fast_z_ctas(g);
+    return f ? f : z_ctas(g);
+}
+template <> int z_ctas_for<double>(const GridDesc& g) { return z_ctas(g); }
+
 template <typename R, typename K>
 static void set_smem(K kern, size_t bytes) {
-    if (bytes > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    // static (2 KB) plus dynamic shared memory above 48 KB needs the opt-in
+    if (bytes > 32 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
 template <typename R>
 void launch_x_forward(const GridDesc& g, int mode, unsigned mask, const R* tau, void* spec,
                       double* partial, cudaStream_t st) {
     using T2 = typename Cplx<R>::T;
+    if constexpr (std::is_same<R, float>::value) {
+        if (fast_x_forward(g, mode, mask, tau, spec, partial, st)) return;
+    }
     const size_t sm = 2ull * g.rows * g.M * sizeof(T2);
     dim3 grid(x_ctas(g), g.nslots);
     T2* sp = reinterpret_cast<T2*>(spec);
@@ -475,6 +420,9 @@ void launch_x_forward(const GridDesc& g, int mode, unsigned mask, const R* tau, 
 template <typename R>
 void launch_y_pass(const GridDesc& g, bool forward, unsigned mask, void* spec, cudaStream_t st) {
     using T2 = typename Cplx<R>::T;
+    if constexpr (std::is_same<R, float>::value) {
+        if (fast_y(g, forward, mask, spec, st)) return;
+    }
     const size_t sm = 2ull * g.N * g.Py * sizeof(T2);
     dim3 grid(3 * g.N * (g.M / g.Py), g.nslots);
     T2* sp = reinterpret_cast<T2*>(spec);
@@ -490,6 +438,9 @@ void launch_y_pass(const GridDesc& g, bool forward, unsigned mask, void* spec, c
 template <typename R>
 void launch_z_pass(const GridDesc& g, int mode, unsigned mask, void* spec, double* partial, cudaStream_t st) {
     using T2 = typename Cplx<R>::T;
+    if constexpr (std::is_same<R, float>::value) {
+        if (fast_z(g, mode, mask, spec, partial, st)) return;
+    }
     const size_t sm = 2ull * 3 * g.N * g.Pz * sizeof(T2);
     dim3 grid(z_ctas(g), g.nslots);
     T2* sp = reinterpret_cast<T2*>(spec);
@@ -521,6 +472,9 @@ template <typename R>
 void launch_x_inverse(const GridDesc& g, int mode, unsigned mask, const void* spec, R* tau,
                       const float* r32, float* d32, float* r32_out, double* partial, cudaStream_t st) {
     using T2 = typename Cplx<R>::T;
+    if constexpr (std::is_same<R, float>::value) {
+        if (fast_x_inverse(g, mode, mask, spec, tau, r32, partial, st)) return;
+    }
     const size_t sm = 2ull * g.rows * g.M * sizeof(T2);
     dim3 grid(x_ctas(g), g.nslots);
     const T2* sp = reinterpret_cast<const T2*>(spec);

@@ -1,0 +1,100 @@
+"""The register-resident FP32 kernels (grid sizes 64, 96, 128, 192, 256) against the
+oracle, including the benchmark's full 256^3 size (one sweep, all voxels compared).
+
+Tolerances as in test_gpu_parity: FP32 transforms 2e-6 of the largest coefficient,
+FP32 sweeps 1e-5 relative, FP32-bulk solves 1e-5 on K and 1e-4 relative L2 on the field.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import em as om
+from paper_1504_07499_gb300 import hmg, inputs as I
+
+from test_gpu_parity import kerr, unpack_spectrum
+
+K3 = I.K_PHASES
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_1504_07499_gb300 import build
+    build.build()
+    c = hmg.Context(0)
+    yield c
+    c.close()
+
+
+@pytest.mark.parametrize("N,count", [(64, 4), (128, 3), (192, 1), (256, 1)])
+def test_fast_fft_forward_inverse(ctx, N, count):
+    rng = np.random.default_rng(N)
+    x = rng.standard_normal((count, N, N, N))
+    ref = np.fft.fftn(x, axes=(1, 2, 3))
+    Z = np.empty((count, N * N * N // 2, 2))
+    hmg.hmg_fft_forward(ctx.handle, N, count, hmg.HMG_FP32_BULK, x, Z)
+    Zc = Z[..., 0] + 1j * Z[..., 1]
+    for i in range(count):
+        full = unpack_spectrum(Zc[i], N)
+        assert np.abs(full - ref[i]).max() < 2e-6 * np.abs(ref[i]).max(), (N, i)
+    back = np.empty_like(x)
+    hmg.hmg_fft_inverse(ctx.handle, N, count, hmg.HMG_FP32_BULK, Z, back)
+    assert np.abs(back / N ** 3 - x).max() < 2e-5 * np.abs(x).max()
+
+
+@pytest.mark.parametrize("N", [64, 96, 128])
+def test_fast_sweeps_match_oracle(ctx, N):
+    sl = I.generate_spheres(N, 20, 0.3)
+    ph = om.voxelize(sl.spheres, 0.3, N)
+    E = np.array([0.3, -1.0, 0.5])
+    rng = np.random.default_rng(N)
+    e0 = E[:, None, None, None] + 0.3 * rng.standard_normal((3, N, N, N))
+    ref = om.em_solve(ph, K3, E, tol=0.0, max_iter=2, record=True, e0=e0)
+    e = e0.copy()
+    eps = hmg.hmg_em_iterate(ctx.handle, ph, N, K3, E, hmg.HMG_FP32_BULK, 2, e)
+    assert np.abs(e - ref.e).max() < 1e-5 * np.abs(ref.e).max()
+    assert np.allclose(eps, ref.eps_comp_hist, rtol=1e-4)
+
+
+def test_fast_equilibrium_fp32(ctx):
+    N = 64
+    ph = I.random_phase_grid(8, N)
+    r = om.em_solve(ph, K3, (0.0, 1.0, 0.0), tol=0.0, max_iter=20)
+    ref_eps, ref_mean = om.equilibrium_residual(np.asarray(K3)[ph], r.e, om.wavevectors(N))
+    eps, flux = hmg.hmg_equilibrium(ctx.handle, ph, N, K3, hmg.HMG_FP32_BULK, np.ascontiguousarray(r.e))
+    assert abs(eps - ref_eps) < 1e-4 * ref_eps
+    assert np.abs(flux + ref_mean).max() < 1e-5 * np.abs(ref_mean).max()
+
+
+def test_fast_bulk_solve_64_matches_oracle(ctx):
+    N = 64
+    sl = I.generate_spheres(1000, 30, 0.2)
+    ph = om.voxelize(sl.spheres, 0.3, N)
+    k = (0.20, 0.25, 40.0)          # contrast 200 keeps the oracle solve short
+    Kref, res = om.effective_tensor(ph, k, tol=1e-8)
+    e = np.empty((3, 3, N, N, N))
+    K, info, _ = hmg.hmg_solve_fields(ctx.handle, ph, N, k, 1e-8, hmg.HMG_FP32_BULK, e)
+    assert kerr(K, Kref) < 1e-5
+    for j in range(3):
+        assert np.linalg.norm(e[j] - res[j].e) < 1e-4 * np.linalg.norm(res[j].e)
+        assert info["eps_eq"][j] < 1e-8
+
+
+def test_full_size_256_one_sweep_matches_oracle(ctx):
+    """The benchmark's grid (256^3, 100 spheres at 40 %, l = 0.3): one sweep from the
+    initial field, every voxel of all three components against the oracle."""
+    N = 256
+    sl = I.generate_spheres(3000, 100, 0.40)
+    ph_d = torch.empty(N ** 3, dtype=torch.uint8, device="cuda")
+    hmg.hmg_voxelize(ctx.handle, torch.from_numpy(np.ascontiguousarray(sl.spheres)).cuda(), 0.3, N, ph_d)
+    ph = ph_d.cpu().numpy().reshape(N, N, N)
+    assert (ph == om.voxelize(sl.spheres, 0.3, N)).all()          # bit-exact at full size
+    E = np.array([1.0, 0.0, 0.0])
+    ref = om.em_solve(ph, K3, E, tol=0.0, max_iter=1, record=True)
+    e = torch.zeros((3, N ** 3), dtype=torch.float64, device="cuda")
+    e[0] = 1.0
+    eps = hmg.hmg_em_iterate(ctx.handle, ph_d, N, K3, E, hmg.HMG_FP32_BULK, 1, e)
+    got = e.cpu().numpy().reshape(3, N, N, N)
+    assert np.abs(got - ref.e).max() < 1e-5 * np.abs(ref.e).max()
+    assert abs(eps[0] - ref.eps_comp_hist[0]) < 1e-5 * ref.eps_comp_hist[0]
