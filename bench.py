@@ -324,6 +324,7 @@ def main() -> None:
             "algorithmic_hbm_frac": value / world * per_vox / (peak * 1e9),
             "kernels": kernels,
             "gpu_launches": launches,
+            "z_variant": hmg.hmg_get_variant(ctx.handle, N_GRID),
             "clocks": clocks,
             "e2e": {"value": e2e_vox / e2e_s if e2e_vox else None, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}}
 

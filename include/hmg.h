@@ -214,6 +214,19 @@ hmg_status hmg_submit(hmg_ctx* ctx, const uint8_t* phase, int N, double k_matrix
  * A finished ticket is released by the call that returns its result. */
 hmg_status hmg_poll(hmg_ctx* ctx, uint64_t ticket, double K_out[9], hmg_info* info);
 
+/* ---- kernel variants (autotuning) --------------------------------------------- */
+
+/* The FP32 path has two z-pass kernels for grid sizes 64, 96, 128, 192 and 256
+ * (variant 0: one thread holds the three components of its modes; variant 1: one
+ * thread group per component, projections summed through shared memory).  The first
+ * FP32 solve at a size times both on the device and keeps the faster.
+ * hmg_set_variant pins `variant` (0 or 1) for size N, or clears the choice (-1) so
+ * that the next solve times them again.  Both give the same results to rounding. */
+hmg_status hmg_set_variant(hmg_ctx* ctx, int N, int variant);
+
+/* The variant chosen for size N (-1 if none yet). */
+hmg_status hmg_get_variant(hmg_ctx* ctx, int N, int* variant);
+
 /* ---- tracing ------------------------------------------------------------------ */
 
 /* Kernel kinds reported by the tracer. */

@@ -153,6 +153,40 @@ GridDesc make_desc(const GridPlan& gp, bool fp64, const double k[3], const uint8
     return g;
 }
 
+int autotune_z(::hmg_ctx* c, GridDesc g, SolveState* s, cudaStream_t st) {
+    auto it = c->ztune.find(g.N);
+    if (it != c->ztune.end()) return it->second;
+    int best = 0;
+    if (!s->spec32 || !fast_z_ctas(g)) {
+        c->ztune[g.N] = best;
+        return best;
+    }
+    const unsigned all = (1u << g.nslots) - 1u;
+    cudaMemsetAsync(s->spec32, 0, (size_t)g.nslots * 3 * g.N3 * sizeof(float), st);
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    float best_ms = 1e30f;
+    for (int v = 0; v < 2; ++v) {
+        g.zvar = v;
+        launch_z_pass<float>(g, Z_ITER, all, s->spec32, nullptr, st);   // warm-up
+        cudaEventRecord(a, st);
+        for (int r = 0; r < 4; ++r) launch_z_pass<float>(g, Z_ITER, all, s->spec32, nullptr, st);
+        cudaEventRecord(b, st);
+        cudaEventSynchronize(b);
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, a, b) == cudaSuccess && ms < best_ms) {
+            best_ms = ms;
+            best = v;
+        }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    cudaGetLastError();
+    c->ztune[g.N] = best;
+    return best;
+}
+
 // ---------------------------------------------------------------------------
 // device buffers
 // ---------------------------------------------------------------------------
@@ -323,7 +357,7 @@ static int popc(unsigned m) { return __builtin_popcount(m); }
 
 template <typename R>
 void Solver::sweep(unsigned mask, R* field, void* spec, int zmode, int ximode, const float* r32in,
-                   float* d32, float* r32out) {
+                   float* d32, float* r32out, int red_off) {
     const double f = (double)popc(mask) * 3.0 * (double)g.N3;   // field elements moved per array
     const double F = sizeof(R);
     HMG_TRACED(HMG_K_X_FORWARD, f * 2 * F + (double)g.N3,
@@ -334,10 +368,12 @@ void Solver::sweep(unsigned mask, R* field, void* spec, int zmode, int ximode, c
     double xb = f * 2 * F;                                       // spectrum in, field out
     if (ximode == XI_INPLACE_RES) xb += f * F;                  // old field for the residual
     if (ximode == XI_ADD_R_RES) xb += f * F + f * 4;            // old field and r
+    if (ximode == XI_ADD_R) xb += f * 4;                         // r
     if (ximode == XI_DIFF) xb = f * F + f * F + 2 * f * 4;      // spectrum, old field, d and r out
     HMG_TRACED(HMG_K_X_INVERSE, xb,
                launch_x_inverse<R>(g, ximode, mask, spec, field, r32in, d32, r32out, s->partial, st));
-    HMG_TRACED(HMG_K_OTHER, 0.0, launch_reduce(s->partial, g.nslots, x_ctas_for<R>(g), 1, s->red, st));
+    if (ximode == XI_INPLACE_RES || ximode == XI_ADD_R_RES || ximode == XI_DIFF)
+        HMG_TRACED(HMG_K_OTHER, 0.0, launch_reduce(s->partial, g.nslots, x_ctas_for<R>(g), 1, s->red + red_off, st));
 }
 
 template <typename R>
@@ -450,7 +486,7 @@ hmg_status Solver::run_bulk(int max_iter, double tol, hmg_info* info, double K[9
     }
     const double thetaA = std::max(tol, 1e-6);
     const double eta = 1e-4;           // inner solves reduce the outer residual by this factor
-    const int stall = 25;              // sweeps without a new best residual = FP32 floor
+    const int stall = 24;              // sweeps without a new best residual = FP32 floor
     auto mask_of = [&](int ph) {
         unsigned m = 0;
         for (int sl = 0; sl < g.nslots; ++sl)
@@ -499,19 +535,29 @@ hmg_status Solver::run_bulk(int max_iter, double tol, hmg_info* info, double K[9
                 }
             continue;
         }
-        // FP32 sweeps: plain (phase A) and defect-correction (inner)
+        // FP32 sweeps, plain (phase A) and defect-correction (inner), in blocks of
+        // `blk` sweeps: only the last sweep of a block reads the old field for the
+        // residual, and the host synchronizes once per block
         unsigned ma = mask_of(PH_A), mi = mask_of(PH_INNER);
-        if (ma) sweep<float>(ma, s->f32buf, s->spec32, Z_ITER, XI_INPLACE_RES, nullptr, nullptr, nullptr);
-        double ha[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
-        if (ma && !fetch(ha, 0, g.nslots)) return HMG_CUDA_ERROR;
-        if (mi) sweep<float>(mi, s->f32buf, s->spec32, Z_ITER_NOB, XI_ADD_R_RES, s->r32, nullptr, nullptr);
-        if (mi && !fetch(hi, 0, g.nslots)) return HMG_CUDA_ERROR;
+        const int blk = std::max(1, std::min(kResidualEvery, max_iter - total + 1));
+        for (int b = 0; b < blk; ++b) {
+            const bool last = b == blk - 1;
+            if (ma)
+                sweep<float>(ma, s->f32buf, s->spec32, Z_ITER, last ? XI_INPLACE_RES : XI_INPLACE, nullptr, nullptr,
+                             nullptr, 0);
+            if (mi)
+                sweep<float>(mi, s->f32buf, s->spec32, Z_ITER_NOB, last ? XI_ADD_R_RES : XI_ADD_R, s->r32, nullptr,
+                             nullptr, 8);
+        }
+        total += blk - 1;
+        double h[16];
+        if (!fetch(h, 0, 16)) return HMG_CUDA_ERROR;
         unsigned to_outer_a = 0, to_outer_i = 0;
         for (int sl = 0; sl < g.nslots; ++sl) {
             const bool a = (ma >> sl) & 1u, in = (mi >> sl) & 1u;
             if (!a && !in) continue;
-            ++iters[sl];
-            eps32[sl] = eps_from_sum(a ? ha[sl] : hi[sl], sl);
+            iters[sl] += blk;
+            eps32[sl] = eps_from_sum(a ? h[sl] : h[8 + sl], sl);
             if (!std::isfinite(eps32[sl])) {
                 status[sl] = HMG_DIVERGED;
                 state[sl] = PH_DONE;
@@ -521,13 +567,13 @@ hmg_status Solver::run_bulk(int max_iter, double tol, hmg_info* info, double K[9
                 best[sl] = eps32[sl];
                 since_best[sl] = 0;
             } else {
-                ++since_best[sl];
+                since_best[sl] += blk;
             }
             if (a) {
                 eps_comp[sl] = eps32[sl];
                 if (eps32[sl] < thetaA || since_best[sl] >= stall) to_outer_a |= 1u << sl;
             } else {
-                ++inner_n[sl];
+                inner_n[sl] += blk;
                 if (eps32[sl] < eta * outer_eps[sl] || since_best[sl] >= stall) to_outer_i |= 1u << sl;
             }
         }
@@ -567,8 +613,8 @@ hmg_status Solver::finish(const int status[3], const int iters[3], const int it6
     return HMG_OK;
 }
 
-template void Solver::sweep<float>(unsigned, float*, void*, int, int, const float*, float*, float*);
-template void Solver::sweep<double>(unsigned, double*, void*, int, int, const float*, float*, float*);
+template void Solver::sweep<float>(unsigned, float*, void*, int, int, const float*, float*, float*, int);
+template void Solver::sweep<double>(unsigned, double*, void*, int, int, const float*, float*, float*, int);
 template bool Solver::check_eq<float>(unsigned, const float*, void*, double*, double (*)[3]);
 template bool Solver::check_eq<double>(unsigned, const double*, void*, double*, double (*)[3]);
 

@@ -80,6 +80,7 @@ hmg_status prepare(hmg_ctx* ctx, const uint8_t* phase, int N, const double k[3],
     hmg_status st = cuda_status(copy_in(ctx->solve.phase, phase, N3, ctx->stream), "phase copy");
     if (st != HMG_OK) return st;
     *g = make_desc(*gp, fp64, k, ctx->solve.phase, nslots);
+    if (!fp64) g->zvar = autotune_z(ctx, *g, &ctx->solve, ctx->stream);
     return HMG_OK;
 }
 
@@ -138,6 +139,28 @@ hmg_status hmg_destroy(hmg_ctx* ctx) {
 }
 
 size_t hmg_footprint(int N, hmg_precision p) { return state_bytes(N, p == HMG_FP64, 3); }
+
+hmg_status hmg_set_variant(hmg_ctx* ctx, int N, int variant) {
+    g_last_error.clear();
+    if (!ctx || !valid_N(N) || variant < -1 || variant > 1) {
+        set_error("bad context, N or variant (-1, 0 or 1)");
+        return HMG_INVALID_ARG;
+    }
+    if (variant < 0) ctx->ztune.erase(N);
+    else ctx->ztune[N] = variant;
+    return HMG_OK;
+}
+
+hmg_status hmg_get_variant(hmg_ctx* ctx, int N, int* variant) {
+    g_last_error.clear();
+    if (!ctx || !variant || !valid_N(N)) {
+        set_error("bad context, N or output");
+        return HMG_INVALID_ARG;
+    }
+    auto it = ctx->ztune.find(N);
+    *variant = it == ctx->ztune.end() ? -1 : it->second;
+    return HMG_OK;
+}
 
 hmg_status hmg_trace_enable(hmg_ctx* ctx, int enable) {
     g_last_error.clear();
@@ -397,6 +420,7 @@ static hmg_status fft_common(hmg_ctx* ctx, int N, int count, hmg_precision preci
     }
     const double k[3] = {1.0, 1.0, 1.0};
     GridDesc g = make_desc(*gp, fp64, k, ctx->solve.phase, 1);
+    if (!fp64) g.zvar = autotune_z(ctx, g, &ctx->solve, ctx->stream);
     SolveState& s = ctx->solve;
     const long long N3 = g.N3;
     double* d64 = s.tau64;          // 3 N^3 doubles: staging of one group of three grids

@@ -174,7 +174,7 @@ __device__ double block_sum_d(double v, double* sh) {
 // ---------------------------------------------------------------------------
 
 template <int L, int P, bool FWD>
-__global__ void __launch_bounds__(P * Split<L>::TP)
+__global__ void __launch_bounds__(P * Split<L>::TP, 3)
 k_fy(GridDesc g, unsigned mask, float2* __restrict__ spec) {
     constexpr int E = Split<L>::E, TP = Split<L>::TP;
     const int slot = blockIdx.y;
@@ -201,32 +201,69 @@ k_fy(GridDesc g, unsigned mask, float2* __restrict__ spec) {
 }
 
 // ---------------------------------------------------------------------------
-// z pass: P consecutive kx columns at one ky, three components per thread
+// z pass: P consecutive kx columns at one ky; three thread groups, one per
+// component.  The Green operator needs, per mode, the projection d . s over the
+// three components: each thread writes its component's share to shared memory,
+// reads the other two, and updates its own component.
 // ---------------------------------------------------------------------------
 
+// Projector data of packed mode (kx, ky, kz) for component c, for the real part
+// (plane kx, or plane 0 of the packed column) and the imaginary part (same plane,
+// or plane N/2 at the four self-conjugate modes of the packed column):
+// integer direction component d and |d|^2 (0 where the projector vanishes).
+__device__ __forceinline__ void mode_parts(int kx, int ky, int kz, int N, int c, int& dA, int& nA, int& dB,
+                                           int& nB) {
+    const int my = signed_mode(ky, N), mz = signed_mode(kz, N);
+    int d[3];
+    if (kx == 0 && (ky == 0 || ky == N / 2) && (kz == 0 || kz == N / 2)) {
+        nA = mode_dir(0, my, mz, N, d);
+        dA = d[c];
+        nB = mode_dir(N / 2, my, mz, N, d);
+        dB = d[c];
+    } else {
+        nA = nB = mode_dir(kx, my, mz, N, d);
+        dA = dB = d[c];
+    }
+}
+
+// Fixed-order CTA sum for any block size (multiple of 32); result valid in thread 0.
+__device__ double block_sum_any(double v, double* sh) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double r = 0.0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) r += sh[w];
+    __syncthreads();
+    return r;
+}
+
+// Variant 0: one thread holds all three components of its (column, pencil part):
+// the Green operator runs entirely in registers (high register count, low occupancy).
 template <int L, int P, int MODE>
-__global__ void __launch_bounds__(P * Split<L>::TP)
-k_fz(GridDesc g, unsigned mask, float2* __restrict__ spec, double* __restrict__ partial) {
+__global__ void __launch_bounds__(P * Split<L>::TP, 3)
+k_fz3(GridDesc g, unsigned mask, float2* __restrict__ spec, double* __restrict__ partial) {
     constexpr int E = Split<L>::E, TP = Split<L>::TP, KPT = E / TP;
     constexpr int NS = xslots<L>() * P;
     const int slot = blockIdx.y;
     if (!((mask >> slot) & 1u)) return;
     extern __shared__ __align__(16) float2 sh[];   // 3 * NS
     __shared__ double red[P * TP];
-    const int N = g.N, M = g.M;
+    constexpr int N = L, M = L / 2;
+    constexpr long long NNM = (long long)N * N * M;
     const int p = threadIdx.x % P, t = threadIdx.x / P;
     const int nkb = M / P;
     const int kb = blockIdx.x % nkb;
     const int ky = blockIdx.x / nkb;
     const int kx = kb * P + p;
-    float2* base = spec + (long long)slot * 3 * g.NNM + (long long)ky * M + kb * P + p;
-    const long long rowz = (long long)N * M;     // stride between z rows
+    float2* base = spec + (long long)slot * 3 * NNM + (long long)ky * M + kb * P + p;
+    constexpr long long rowz = (long long)N * M;     // stride between z rows
     const float2* twL = g.tw32 + g.pN.tw_off;
     float2 v[3][E];
 #pragma unroll
     for (int c = 0; c < 3; ++c)
 #pragma unroll
-        for (int n1 = 0; n1 < E; ++n1) v[c][n1] = base[c * g.NNM + (long long)(TP * n1 + t) * rowz];
+        for (int n1 = 0; n1 < E; ++n1) v[c][n1] = base[c * NNM + (long long)(TP * n1 + t) * rowz];
 
     if (MODE == Z_INV) {
         // plain inverse transform of each component (natural order in and out)
@@ -249,7 +286,7 @@ k_fz(GridDesc g, unsigned mask, float2* __restrict__ spec, double* __restrict__ 
             for (int i = 0; i < KPT; ++i)
 #pragma unroll
                 for (int k2 = 0; k2 < TP; ++k2)
-                    base[c * g.NNM + (long long)(t * KPT + i + E * k2) * rowz] = v[c][i * TP + k2];
+                    base[c * NNM + (long long)(t * KPT + i + E * k2) * rowz] = v[c][i * TP + k2];
         return;
     }
     if (MODE == Z_EQ) {
@@ -283,7 +320,111 @@ k_fz(GridDesc g, unsigned mask, float2* __restrict__ spec, double* __restrict__ 
 #pragma unroll
     for (int c = 0; c < 3; ++c)
 #pragma unroll
-        for (int n1 = 0; n1 < E; ++n1) base[c * g.NNM + (long long)(TP * n1 + t) * rowz] = v[c][n1];
+        for (int n1 = 0; n1 < E; ++n1) base[c * NNM + (long long)(TP * n1 + t) * rowz] = v[c][n1];
+}
+
+// Variant 1: three thread groups, one per component; the projection d . s is summed
+// through shared memory (more threads, fewer registers per thread).
+template <int L, int P, int MODE>
+__global__ void __launch_bounds__(3 * P * Split<L>::TP, 1)
+k_fzs(GridDesc g, unsigned mask, float2* __restrict__ spec, double* __restrict__ partial) {
+    constexpr int E = Split<L>::E, TP = Split<L>::TP, KPT = E / TP;
+    constexpr int NS = xslots<L>() * P;
+    const int slot = blockIdx.y;
+    if (!((mask >> slot) & 1u)) return;
+    extern __shared__ __align__(16) float2 sh[];   // 3 * NS
+    __shared__ double red[3 * P * Split<L>::TP / 32 + 1];
+    constexpr int N = L, M = L / 2;
+    constexpr long long NNM = (long long)N * N * M;
+    const int lt = threadIdx.x % (P * TP), c = threadIdx.x / (P * TP);
+    const int p = lt % P, t = lt / P;
+    const int nkb = M / P;
+    const int kb = blockIdx.x % nkb;
+    const int ky = blockIdx.x / nkb;
+    const int kx = kb * P + p;
+    float2* base = spec + (long long)slot * 3 * NNM + c * NNM + (long long)ky * M + kb * P + p;
+    constexpr long long rowz = (long long)N * M;     // stride between z rows
+    const float2* twL = g.tw32 + g.pN.tw_off;
+    float2* shc = sh + c * NS + p;
+    float2 v[E];
+#pragma unroll
+    for (int n1 = 0; n1 < E; ++n1) v[n1] = base[(long long)(TP * n1 + t) * rowz];
+
+    if (MODE == Z_INV) {
+        stage1_write<L, false>(v, t, twL, shc, P);
+        __syncthreads();
+        stage2_read<L, false>(v, t, shc, P);
+    } else {
+        stage1_write<L, true>(v, t, twL, shc, P);
+        __syncthreads();
+        stage2_read<L, true>(v, t, shc, P);
+    }
+    if (MODE == Z_FWD || MODE == Z_INV) {
+#pragma unroll
+        for (int i = 0; i < KPT; ++i)
+#pragma unroll
+            for (int k2 = 0; k2 < TP; ++k2) base[(long long)(t * KPT + i + E * k2) * rowz] = v[i * TP + k2];
+        return;
+    }
+    // share of d . s of this component, one slot per (t, value) of the thread group
+    __syncthreads();   // every thread has read the forward exchange
+#pragma unroll
+    for (int i = 0; i < KPT; ++i)
+#pragma unroll
+        for (int k2 = 0; k2 < TP; ++k2) {
+            int dA, nA, dB, nB;
+            mode_parts(kx, ky, t * KPT + i + E * k2, N, c, dA, nA, dB, nB);
+            const float2 x = v[i * TP + k2];
+            shc[((i * TP + k2) * TP + t) * P] = make_float2((float)dA * x.x, (float)dB * x.y);
+        }
+    __syncthreads();
+    const float2* sh1 = sh + ((c + 1) % 3) * NS + p;
+    const float2* sh2 = sh + ((c + 2) % 3) * NS + p;
+    if (MODE == Z_EQ) {
+        double acc = 0.0;
+        if (c == 0) {
+#pragma unroll
+            for (int i = 0; i < KPT; ++i)
+#pragma unroll
+                for (int k2 = 0; k2 < TP; ++k2) {
+                    const int q = ((i * TP + k2) * TP + t) * P;
+                    const float2 a = shc[q], b = sh1[q], e = sh2[q];
+                    const double dx = (double)a.x + (double)b.x + (double)e.x;
+                    const double dy = (double)a.y + (double)b.y + (double)e.y;
+                    const int kz = t * KPT + i + E * k2;
+                    const bool special = (kx == 0) && (ky == 0 || ky == N / 2) && (kz == 0 || kz == N / 2);
+                    acc += (kx == 0 || special ? 1.0 : 2.0) * (dx * dx + dy * dy);
+                }
+        }
+        const double twopi_n = 6.283185307179586476925 / (double)N;
+        const double sm = block_sum_any(acc, red) * twopi_n * twopi_n / ((double)g.N3 * (double)g.N3);
+        if (threadIdx.x == 0) partial[(long long)slot * gridDim.x + blockIdx.x] = sm;
+        return;
+    }
+    const float scale = (float)(1.0 / (double)g.N3);
+    const float twok0E = (float)(2.0 * g.k0 * g.E[slot][c]);
+#pragma unroll
+    for (int i = 0; i < KPT; ++i)
+#pragma unroll
+        for (int k2 = 0; k2 < TP; ++k2) {
+            const int kz = t * KPT + i + E * k2;
+            int dA, nA, dB, nB;
+            mode_parts(kx, ky, kz, N, c, dA, nA, dB, nB);
+            const int q = ((i * TP + k2) * TP + t) * P;
+            const float2 a = shc[q], b = sh1[q], e = sh2[q];
+            const float dotA = a.x + b.x + e.x, dotB = a.y + b.y + e.y;
+            const float fA = nA > 0 ? 2.0f / (float)nA : 0.0f, fB = nB > 0 ? 2.0f / (float)nB : 0.0f;
+            float2& x = v[i * TP + k2];
+            x.x = scale * (x.x - fA * (float)dA * dotA);
+            x.y = scale * (x.y - fB * (float)dB * dotB);
+            if (MODE == Z_ITER && kx == 0 && ky == 0 && kz == 0) x.x += twok0E;
+        }
+    __syncthreads();   // every thread has read the shares
+    rstage2_write<L>(v, t, twL, shc, P);
+    __syncthreads();
+    rstage1_read<L>(v, t, shc, P);
+#pragma unroll
+    for (int n1 = 0; n1 < E; ++n1) base[(long long)(TP * n1 + t) * rowz] = v[n1];
 }
 
 // ---------------------------------------------------------------------------
@@ -297,7 +438,7 @@ template <int M> constexpr int row_stride() {
 }
 
 template <int M, int RW, int MODE>
-__global__ void __launch_bounds__(RW * Split<M>::TP)
+__global__ void __launch_bounds__(RW * Split<M>::TP, 4)
 k_fx_forward(GridDesc g, unsigned mask, const float* __restrict__ tau, float2* __restrict__ spec,
              double* __restrict__ partial) {
     constexpr int E = Split<M>::E, TP = Split<M>::TP, KPT = E / TP, RS = row_stride<M>();
@@ -363,7 +504,7 @@ k_fx_forward(GridDesc g, unsigned mask, const float* __restrict__ tau, float2* _
 }
 
 template <int M, int RW, int MODE>
-__global__ void __launch_bounds__(RW * Split<M>::TP)
+__global__ void __launch_bounds__(RW * Split<M>::TP, 3)
 k_fx_inverse(GridDesc g, unsigned mask, const float2* __restrict__ spec, float* __restrict__ tau,
              const float* __restrict__ r32, double* __restrict__ partial) {
     constexpr int E = Split<M>::E, TP = Split<M>::TP, KPT = E / TP, RS = row_stride<M>();
@@ -382,7 +523,7 @@ k_fx_inverse(GridDesc g, unsigned mask, const float2* __restrict__ spec, float* 
 #pragma unroll
         for (int j = 0; j < E; ++j) old[j] = out[t + TP * j];
     }
-    if (MODE == XI_ADD_R_RES) {
+    if (MODE == XI_ADD_R_RES || MODE == XI_ADD_R) {
         const float2* rr = reinterpret_cast<const float2*>(r32 + fbase);
 #pragma unroll
         for (int j = 0; j < E; ++j) radd[j] = rr[t + TP * j];
@@ -427,7 +568,7 @@ k_fx_inverse(GridDesc g, unsigned mask, const float2* __restrict__ spec, float* 
 #pragma unroll
     for (int j = 0; j < E; ++j) {
         float2 x = rs[t + TP * j];
-        if (MODE == XI_ADD_R_RES) {
+        if (MODE == XI_ADD_R_RES || MODE == XI_ADD_R) {
             x.x += radd[j].x;
             x.y += radd[j].y;
         }
@@ -457,8 +598,13 @@ void launch_dyn(K kern, dim3 grid, int threads, size_t bytes, cudaStream_t st, A
     if (bytes > 32 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     kern<<<grid, threads, bytes, st>>>(args...);
 }
-template <int L> constexpr int fy_cols() { return 256 / fast::Split<L>::TP; }
-template <int L> constexpr int fz_cols() { return 128 / fast::Split<L>::TP; }
+constexpr int pow2_cols(int cap, int M) {
+    int p = 1;
+    while (p * 2 <= cap && M % (p * 2) == 0) p *= 2;
+    return p;
+}
+template <int L> constexpr int fy_cols() { return pow2_cols(256 / fast::Split<L>::TP, L / 2); }
+template <int L> constexpr int fz_cols() { return pow2_cols(128 / fast::Split<L>::TP, L / 2); }
 template <int M> constexpr int fx_rows() { return 256 / fast::Split<M>::TP; }
 }  // namespace
 
@@ -506,16 +652,27 @@ bool fast_z(const GridDesc& g, int mode, unsigned mask, void* spec, double* part
 #define FZ(L)                                                                                          \
     {                                                                                                  \
         constexpr int P = fz_cols<L>();                                                                \
-        constexpr int T = P * fast::Split<L>::TP;                                                      \
         if (g.M % P) return false;                                                                     \
         dim3 grid(g.N * (g.M / P), g.nslots);                                                          \
         const size_t sm = sizeof(float2) * 3 * fast::xslots<L>() * P;                                  \
-        switch (mode) {                                                                                \
-            case Z_FWD: launch_dyn(fast::k_fz<L, P, Z_FWD>, grid, T, sm, st, g, mask, sp, partial); break;   \
-            case Z_INV: launch_dyn(fast::k_fz<L, P, Z_INV>, grid, T, sm, st, g, mask, sp, partial); break;   \
-            case Z_ITER: launch_dyn(fast::k_fz<L, P, Z_ITER>, grid, T, sm, st, g, mask, sp, partial); break; \
-            case Z_ITER_NOB: launch_dyn(fast::k_fz<L, P, Z_ITER_NOB>, grid, T, sm, st, g, mask, sp, partial); break; \
-            default: launch_dyn(fast::k_fz<L, P, Z_EQ>, grid, T, sm, st, g, mask, sp, partial); break;       \
+        if (g.zvar == 1) {                                                                             \
+            constexpr int T = 3 * P * fast::Split<L>::TP;                                              \
+            switch (mode) {                                                                            \
+                case Z_FWD: launch_dyn(fast::k_fzs<L, P, Z_FWD>, grid, T, sm, st, g, mask, sp, partial); break;   \
+                case Z_INV: launch_dyn(fast::k_fzs<L, P, Z_INV>, grid, T, sm, st, g, mask, sp, partial); break;   \
+                case Z_ITER: launch_dyn(fast::k_fzs<L, P, Z_ITER>, grid, T, sm, st, g, mask, sp, partial); break; \
+                case Z_ITER_NOB: launch_dyn(fast::k_fzs<L, P, Z_ITER_NOB>, grid, T, sm, st, g, mask, sp, partial); break; \
+                default: launch_dyn(fast::k_fzs<L, P, Z_EQ>, grid, T, sm, st, g, mask, sp, partial); break;       \
+            }                                                                                          \
+        } else {                                                                                       \
+            constexpr int T = P * fast::Split<L>::TP;                                                  \
+            switch (mode) {                                                                            \
+                case Z_FWD: launch_dyn(fast::k_fz3<L, P, Z_FWD>, grid, T, sm, st, g, mask, sp, partial); break;   \
+                case Z_INV: launch_dyn(fast::k_fz3<L, P, Z_INV>, grid, T, sm, st, g, mask, sp, partial); break;   \
+                case Z_ITER: launch_dyn(fast::k_fz3<L, P, Z_ITER>, grid, T, sm, st, g, mask, sp, partial); break; \
+                case Z_ITER_NOB: launch_dyn(fast::k_fz3<L, P, Z_ITER_NOB>, grid, T, sm, st, g, mask, sp, partial); break; \
+                default: launch_dyn(fast::k_fz3<L, P, Z_EQ>, grid, T, sm, st, g, mask, sp, partial); break;       \
+            }                                                                                          \
         }                                                                                              \
     }
     switch (g.N) {
@@ -572,7 +729,8 @@ bool fast_x_inverse(const GridDesc& g, int mode, unsigned mask, const void* spec
                     double* partial, cudaStream_t st) {
     const float2* sp = reinterpret_cast<const float2*>(spec);
     if (!fast_x_ctas(g)) return false;
-    if (mode != XI_PLAIN && mode != XI_INPLACE && mode != XI_INPLACE_RES && mode != XI_ADD_R_RES) return false;
+    if (mode != XI_PLAIN && mode != XI_INPLACE && mode != XI_INPLACE_RES && mode != XI_ADD_R_RES && mode != XI_ADD_R)
+        return false;
 #define FXI(M)                                                                                                         \
     {                                                                                                                  \
         constexpr int RW = fx_rows<M>();                                                                               \
@@ -581,6 +739,7 @@ bool fast_x_inverse(const GridDesc& g, int mode, unsigned mask, const void* spec
         const size_t sm = sizeof(float2) * RW * fast::row_stride<M>();                                                 \
         if (mode == XI_INPLACE_RES) launch_dyn(fast::k_fx_inverse<M, RW, XI_INPLACE_RES>, grid, T, sm, st, g, mask, sp, tau, r32, partial); \
         else if (mode == XI_ADD_R_RES) launch_dyn(fast::k_fx_inverse<M, RW, XI_ADD_R_RES>, grid, T, sm, st, g, mask, sp, tau, r32, partial); \
+        else if (mode == XI_ADD_R) launch_dyn(fast::k_fx_inverse<M, RW, XI_ADD_R>, grid, T, sm, st, g, mask, sp, tau, r32, partial); \
         else launch_dyn(fast::k_fx_inverse<M, RW, XI_INPLACE>, grid, T, sm, st, g, mask, sp, tau, r32, partial);        \
     }
     switch (g.M) {

@@ -37,11 +37,12 @@ struct GridDesc {
     int nslots;            // right-hand sides held in the fields
     int rows;              // x-pass rows per CTA
     int Py, Pz;            // columns per CTA in the y and z passes
+    int zvar;              // z-pass kernel variant of the register-resident path (autotuned)
     const uint8_t* phase;  // N^3 phase ids
 };
 
 enum XFwdMode { XF_PLAIN = 0, XF_POLARIZE = 1, XF_FLUX = 2 };
-enum XInvMode { XI_PLAIN = 0, XI_INPLACE = 1, XI_INPLACE_RES = 2, XI_ADD_R_RES = 3, XI_DIFF = 4 };
+enum XInvMode { XI_PLAIN = 0, XI_INPLACE = 1, XI_INPLACE_RES = 2, XI_ADD_R_RES = 3, XI_DIFF = 4, XI_ADD_R = 5 };
 enum ZMode { Z_FWD = 0, Z_INV = 1, Z_ITER = 2, Z_ITER_NOB = 3, Z_EQ = 4 };
 
 // Launch wrappers (hmg_kernels.cu).  `mask` selects the active right-hand sides;
@@ -55,7 +56,7 @@ void launch_y_pass(const GridDesc& g, bool forward, unsigned mask, void* spec, c
 template <typename R>
 void launch_z_pass(const GridDesc& g, int mode, unsigned mask, void* spec, double* partial,
                    cudaStream_t st);
-// x inverse: writes tau (INPLACE*), adds r (ADD_R_RES), or writes d = new - old to
+// x inverse: writes tau (INPLACE*), adds r (ADD_R, ADD_R_RES), or writes d = new - old to
 // d32 and r32 without touching tau (DIFF).  Residual modes add (new-old)^2 per CTA.
 template <typename R>
 void launch_x_inverse(const GridDesc& g, int mode, unsigned mask, const void* spec, R* tau,

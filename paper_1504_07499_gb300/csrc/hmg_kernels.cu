@@ -171,6 +171,11 @@ k_x_inverse(GridDesc g, unsigned mask, const typename Cplx<R>::T* __restrict__ s
             const double da = (double)v.x - (double)o.x, db = (double)v.y - (double)o.y;
             acc += da * da + db * db;
             out[q] = v;
+        } else if (MODE == XI_ADD_R) {
+            const float2 rv = reinterpret_cast<const float2*>(r32 + fbase)[q];
+            v.x += R(rv.x);
+            v.y += R(rv.y);
+            out[q] = v;
         } else if (MODE == XI_ADD_R_RES) {
             const float2 rv = reinterpret_cast<const float2*>(r32 + fbase)[q];
             v.x += R(rv.x);
@@ -486,6 +491,7 @@ void launch_x_inverse(const GridDesc& g, int mode, unsigned mask, const void* sp
         case XI_INPLACE: HMG_XI(XI_INPLACE); break;
         case XI_INPLACE_RES: HMG_XI(XI_INPLACE_RES); break;
         case XI_ADD_R_RES: HMG_XI(XI_ADD_R_RES); break;
+        case XI_ADD_R: HMG_XI(XI_ADD_R); break;
         default: HMG_XI(XI_DIFF); break;
     }
 #undef HMG_XI

@@ -53,6 +53,10 @@ struct SolveState {
 
 GridDesc make_desc(const GridPlan& gp, bool fp64, const double k[3], const uint8_t* phase_d, int nslots);
 
+// Pick the faster z-pass variant of the FP32 register-resident path for g.N by timing
+// both on the state's spectrum buffer (its contents are scratch); cached per context.
+int autotune_z(::hmg_ctx* c, GridDesc g, SolveState* s, cudaStream_t st);
+
 // Per-kernel CUDA-event timing of the solver's launches.
 struct Tracer {
     bool on = false;
@@ -74,15 +78,20 @@ struct Tracer {
     ~Tracer();
 };
 
+// FP32 sweeps of the bulk solver run in blocks of this many; the last sweep of a
+// block computes the residual and the host reads it once per block.
+constexpr int kResidualEvery = 4;
+
 // Driver of one solve on one SolveState.
 struct Solver {
     GridDesc g;
     SolveState* s;
     cudaStream_t st;
     Tracer* tr = nullptr;
+    // one sweep of steps 2-7; residual modes leave the per-slot sums at red[red_off + slot]
     template <typename R>
     void sweep(unsigned mask, R* field, void* spec, int zmode, int ximode, const float* r32in, float* d32,
-               float* r32out);
+               float* r32out, int red_off = 0);
     template <typename R>
     void equilibrium(unsigned mask, const R* field, void* spec);
     template <typename R>
@@ -113,6 +122,7 @@ struct hmg_ctx {
     void release(void* p);
     hmg::Server* server = nullptr;
     hmg::Tracer tracer;
+    std::map<int, int> ztune;   // autotuned z-pass variant per grid size (FP32 path)
 };
 
 namespace hmg {

@@ -27,8 +27,18 @@ def ctx():
     c.close()
 
 
+@pytest.fixture(params=[0, 1], ids=["zvar0", "zvar1"])
+def zvar(request, ctx):
+    """Runs a test once per z-pass kernel variant, pinned for every fast size."""
+    for n in (64, 96, 128, 192, 256):
+        hmg.hmg_set_variant(ctx.handle, n, request.param)
+    yield request.param
+    for n in (64, 96, 128, 192, 256):
+        hmg.hmg_set_variant(ctx.handle, n, -1)
+
+
 @pytest.mark.parametrize("N,count", [(64, 4), (128, 3), (192, 1), (256, 1)])
-def test_fast_fft_forward_inverse(ctx, N, count):
+def test_fast_fft_forward_inverse(ctx, zvar, N, count):
     rng = np.random.default_rng(N)
     x = rng.standard_normal((count, N, N, N))
     ref = np.fft.fftn(x, axes=(1, 2, 3))
@@ -44,7 +54,7 @@ def test_fast_fft_forward_inverse(ctx, N, count):
 
 
 @pytest.mark.parametrize("N", [64, 96, 128])
-def test_fast_sweeps_match_oracle(ctx, N):
+def test_fast_sweeps_match_oracle(ctx, zvar, N):
     sl = I.generate_spheres(N, 20, 0.3)
     ph = om.voxelize(sl.spheres, 0.3, N)
     E = np.array([0.3, -1.0, 0.5])
@@ -57,7 +67,7 @@ def test_fast_sweeps_match_oracle(ctx, N):
     assert np.allclose(eps, ref.eps_comp_hist, rtol=1e-4)
 
 
-def test_fast_equilibrium_fp32(ctx):
+def test_fast_equilibrium_fp32(ctx, zvar):
     N = 64
     ph = I.random_phase_grid(8, N)
     r = om.em_solve(ph, K3, (0.0, 1.0, 0.0), tol=0.0, max_iter=20)
@@ -67,7 +77,7 @@ def test_fast_equilibrium_fp32(ctx):
     assert np.abs(flux + ref_mean).max() < 1e-5 * np.abs(ref_mean).max()
 
 
-def test_fast_bulk_solve_64_matches_oracle(ctx):
+def test_fast_bulk_solve_64_matches_oracle(ctx, zvar):
     N = 64
     sl = I.generate_spheres(1000, 30, 0.2)
     ph = om.voxelize(sl.spheres, 0.3, N)
@@ -81,7 +91,7 @@ def test_fast_bulk_solve_64_matches_oracle(ctx):
         assert info["eps_eq"][j] < 1e-8
 
 
-def test_full_size_256_one_sweep_matches_oracle(ctx):
+def test_full_size_256_one_sweep_matches_oracle(ctx, zvar):
     """The benchmark's grid (256^3, 100 spheres at 40 %, l = 0.3): one sweep from the
     initial field, every voxel of all three components against the oracle."""
     N = 256
@@ -98,3 +108,14 @@ def test_full_size_256_one_sweep_matches_oracle(ctx):
     got = e.cpu().numpy().reshape(3, N, N, N)
     assert np.abs(got - ref.e).max() < 1e-5 * np.abs(ref.e).max()
     assert abs(eps[0] - ref.eps_comp_hist[0]) < 1e-5 * ref.eps_comp_hist[0]
+
+
+def test_autotuner_records_a_variant(ctx):
+    N = 128
+    hmg.hmg_set_variant(ctx.handle, N, -1)
+    assert hmg.hmg_get_variant(ctx.handle, N) == -1
+    ph = I.random_phase_grid(3, N)
+    e = np.zeros((3, N, N, N))
+    e[0] = 1.0
+    hmg.hmg_em_iterate(ctx.handle, ph, N, K3, (1.0, 0.0, 0.0), hmg.HMG_FP32_BULK, 1, e)
+    assert hmg.hmg_get_variant(ctx.handle, N) in (0, 1)
