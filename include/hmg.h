@@ -201,8 +201,12 @@ hmg_status hmg_solve_batch(hmg_ctx* ctx, int count, const uint8_t* const* phases
                            hmg_info* info);
 
 /* Queue one solve request (copies the phase grid; returns without waiting for the
- * GPU).  Requests run concurrently as device memory and slots allow (admission by
- * HBM footprint against the context's budget).  *ticket identifies the request.
+ * GPU).  A worker thread with its own CUDA stream runs the request loop: between
+ * engine ticks it retires finished requests (freeing their device state) and admits
+ * queued ones while their footprint (hmg_footprint) fits the context's budget, up to
+ * 64 at once; every tick advances all admitted HMG_FP32_BULK requests together in one
+ * CUDA-graph launch (continuous batching).  HMG_FP64 requests run one at a time.
+ * *ticket identifies the request.
  * Returns HMG_BUSY when the queue is full, HMG_INVALID_ARG for bad arguments, and
  * HMG_OUT_OF_MEMORY when the request alone exceeds the budget. */
 hmg_status hmg_submit(hmg_ctx* ctx, const uint8_t* phase, int N, double k_matrix,
@@ -250,6 +254,11 @@ hmg_status hmg_trace_enable(hmg_ctx* ctx, int enable);
  * algorithmic bytes those launches had to move (fields read and written once each). */
 hmg_status hmg_trace_read(hmg_ctx* ctx, int kind, double* total_ms, long long* launches,
                           double* algo_bytes);
+
+/* Request-loop counters (zeros before the first hmg_submit): out[0] submitted,
+ * out[1] completed, out[2] most requests resident on the device at once, out[3]
+ * engine ticks, out[4] CUDA-graph captures, out[5] CUDA-graph launches. */
+hmg_status hmg_server_stats(hmg_ctx* ctx, long long out[6]);
 
 /* Device memory the solver state of one N^3 request occupies (bytes). */
 size_t hmg_footprint(int N, hmg_precision precision);

@@ -178,7 +178,7 @@ __global__ void __launch_bounds__(P * Split<L>::TP, 3)
 k_fy(GridDesc g, unsigned mask, float2* __restrict__ spec) {
     constexpr int E = Split<L>::E, TP = Split<L>::TP;
     const int slot = blockIdx.y;
-    if (!((mask >> slot) & 1u)) return;
+    if (!slot_active(g, mask, slot)) return;
     extern __shared__ __align__(16) float2 sh[];   // xslots<L>() * P
     const int M = g.M;
     const int p = threadIdx.x % P, t = threadIdx.x / P;
@@ -246,7 +246,7 @@ k_fz3(GridDesc g, unsigned mask, float2* __restrict__ spec, double* __restrict__
     constexpr int E = Split<L>::E, TP = Split<L>::TP, KPT = E / TP;
     constexpr int NS = xslots<L>() * P;
     const int slot = blockIdx.y;
-    if (!((mask >> slot) & 1u)) return;
+    if (!slot_active(g, mask, slot)) return;
     extern __shared__ __align__(16) float2 sh[];   // 3 * NS
     __shared__ double red[P * TP];
     constexpr int N = L, M = L / 2;
@@ -302,6 +302,7 @@ k_fz3(GridDesc g, unsigned mask, float2* __restrict__ spec, double* __restrict__
         return;
     }
     // Green operator on the registers, then the inverse back to natural order
+    const bool addb = g.dflags ? (g.dflags[slot] & SF_ADDB) != 0 : MODE == Z_ITER;
     const float scale = (float)(1.0 / (double)g.N3);
     const float twok0E[3] = {(float)(2.0 * g.k0 * g.E[slot][0]), (float)(2.0 * g.k0 * g.E[slot][1]),
                              (float)(2.0 * g.k0 * g.E[slot][2])};
@@ -309,7 +310,7 @@ k_fz3(GridDesc g, unsigned mask, float2* __restrict__ spec, double* __restrict__
     for (int i = 0; i < KPT; ++i)
 #pragma unroll
         for (int k2 = 0; k2 < TP; ++k2)
-            green_mode<float>(kx, ky, t * KPT + i + E * k2, N, scale, MODE == Z_ITER, twok0E, v[0][i * TP + k2],
+            green_mode<float>(kx, ky, t * KPT + i + E * k2, N, scale, addb, twok0E, v[0][i * TP + k2],
                               v[1][i * TP + k2], v[2][i * TP + k2]);
     __syncthreads();   // every thread has read the forward exchange
 #pragma unroll
@@ -331,7 +332,7 @@ k_fzs(GridDesc g, unsigned mask, float2* __restrict__ spec, double* __restrict__
     constexpr int E = Split<L>::E, TP = Split<L>::TP, KPT = E / TP;
     constexpr int NS = xslots<L>() * P;
     const int slot = blockIdx.y;
-    if (!((mask >> slot) & 1u)) return;
+    if (!slot_active(g, mask, slot)) return;
     extern __shared__ __align__(16) float2 sh[];   // 3 * NS
     __shared__ double red[3 * P * Split<L>::TP / 32 + 1];
     constexpr int N = L, M = L / 2;
@@ -401,6 +402,7 @@ k_fzs(GridDesc g, unsigned mask, float2* __restrict__ spec, double* __restrict__
         if (threadIdx.x == 0) partial[(long long)slot * gridDim.x + blockIdx.x] = sm;
         return;
     }
+    const bool addb = g.dflags ? (g.dflags[slot] & SF_ADDB) != 0 : MODE == Z_ITER;
     const float scale = (float)(1.0 / (double)g.N3);
     const float twok0E = (float)(2.0 * g.k0 * g.E[slot][c]);
 #pragma unroll
@@ -417,7 +419,7 @@ k_fzs(GridDesc g, unsigned mask, float2* __restrict__ spec, double* __restrict__
             float2& x = v[i * TP + k2];
             x.x = scale * (x.x - fA * (float)dA * dotA);
             x.y = scale * (x.y - fB * (float)dB * dotB);
-            if (MODE == Z_ITER && kx == 0 && ky == 0 && kz == 0) x.x += twok0E;
+            if (addb && kx == 0 && ky == 0 && kz == 0) x.x += twok0E;
         }
     __syncthreads();   // every thread has read the shares
     rstage2_write<L>(v, t, twL, shc, P);
@@ -443,7 +445,7 @@ k_fx_forward(GridDesc g, unsigned mask, const float* __restrict__ tau, float2* _
              double* __restrict__ partial) {
     constexpr int E = Split<M>::E, TP = Split<M>::TP, KPT = E / TP, RS = row_stride<M>();
     const int slot = blockIdx.y;
-    if (!((mask >> slot) & 1u)) return;
+    if (!slot_active(g, mask, slot)) return;
     extern __shared__ __align__(16) float2 sh[];   // RW * RS
     __shared__ double red[RW * TP];
     const int N = g.N;
@@ -509,7 +511,7 @@ k_fx_inverse(GridDesc g, unsigned mask, const float2* __restrict__ spec, float* 
              const float* __restrict__ r32, double* __restrict__ partial) {
     constexpr int E = Split<M>::E, TP = Split<M>::TP, KPT = E / TP, RS = row_stride<M>();
     const int slot = blockIdx.y;
-    if (!((mask >> slot) & 1u)) return;
+    if (!slot_active(g, mask, slot)) return;
     extern __shared__ __align__(16) float2 sh[];   // RW * RS
     __shared__ double red[RW * TP];
     const int N = g.N;
@@ -518,12 +520,16 @@ k_fx_inverse(GridDesc g, unsigned mask, const float2* __restrict__ spec, float* 
     const long long fbase = (long long)slot * 3 * g.N3 + row * N;
     float2* out = reinterpret_cast<float2*>(tau + fbase);
     // prefetch the old field (and r) for the output step: in flight during the FFT
+    constexpr bool kRes = MODE == XI_INPLACE_RES || MODE == XI_ADD_R_RES;
+    constexpr bool kAddR = MODE == XI_ADD_R_RES || MODE == XI_ADD_R;
+    const bool res = kRes && (g.dflags ? g.resid != 0 : true);
+    const bool addr = kAddR && (g.dflags ? (g.dflags[slot] & SF_ADDR) != 0 : true);
     float2 old[E], radd[E];
-    if (MODE == XI_INPLACE_RES || MODE == XI_ADD_R_RES) {
+    if (res) {
 #pragma unroll
         for (int j = 0; j < E; ++j) old[j] = out[t + TP * j];
     }
-    if (MODE == XI_ADD_R_RES || MODE == XI_ADD_R) {
+    if (addr) {
         const float2* rr = reinterpret_cast<const float2*>(r32 + fbase);
 #pragma unroll
         for (int j = 0; j < E; ++j) radd[j] = rr[t + TP * j];
@@ -568,19 +574,19 @@ k_fx_inverse(GridDesc g, unsigned mask, const float2* __restrict__ spec, float* 
 #pragma unroll
     for (int j = 0; j < E; ++j) {
         float2 x = rs[t + TP * j];
-        if (MODE == XI_ADD_R_RES || MODE == XI_ADD_R) {
+        if (addr) {
             x.x += radd[j].x;
             x.y += radd[j].y;
         }
-        if (MODE == XI_INPLACE_RES || MODE == XI_ADD_R_RES) {
+        if (res) {
             const float da = x.x - old[j].x, db = x.y - old[j].y;
             acc += da * da + db * db;
         }
         out[t + TP * j] = x;
     }
-    if (MODE == XI_INPLACE_RES || MODE == XI_ADD_R_RES) {
+    if (kRes) {   // uniform across the CTA (kernel argument and per-slot flag)
         const double s = block_sum_d((double)acc, red);
-        if (threadIdx.x == 0) partial[(long long)slot * gridDim.x + blockIdx.x] = s;
+        if (threadIdx.x == 0 && res) partial[(long long)slot * gridDim.x + blockIdx.x] = s;
     }
 }
 

@@ -38,8 +38,22 @@ struct GridDesc {
     int rows;              // x-pass rows per CTA
     int Py, Pz;            // columns per CTA in the y and z passes
     int zvar;              // z-pass kernel variant of the register-resident path (autotuned)
+    // Per-slot flags in device memory (engine launches; nullptr = use the launch's
+    // mask and template modes): SF_ACTIVE, SF_ADDB (add 2 k0 E at DC, plain sweep),
+    // SF_ADDR (add the defect r, correction sweep).  `resid`: this launch of the x
+    // inverse also reads the old field and sums the residual (flags mode only).
+    const int* dflags;
+    int resid;
     const uint8_t* phase;  // N^3 phase ids
 };
+
+enum SlotFlags { SF_ACTIVE = 1, SF_ADDB = 2, SF_ADDR = 4 };
+
+#ifdef __CUDACC__
+__device__ __forceinline__ bool slot_active(const GridDesc& g, unsigned mask, int slot) {
+    return g.dflags ? (g.dflags[slot] & SF_ACTIVE) != 0 : ((mask >> slot) & 1u) != 0;
+}
+#endif
 
 enum XFwdMode { XF_PLAIN = 0, XF_POLARIZE = 1, XF_FLUX = 2 };
 enum XInvMode { XI_PLAIN = 0, XI_INPLACE = 1, XI_INPLACE_RES = 2, XI_ADD_R_RES = 3, XI_DIFF = 4, XI_ADD_R = 5 };

@@ -59,7 +59,7 @@ k_x_forward(GridDesc g, unsigned mask, const R* __restrict__ tau, typename Cplx<
             double* __restrict__ partial) {
     using T2 = typename Cplx<R>::T;
     const int slot = blockIdx.y;
-    if (!((mask >> slot) & 1u)) return;
+    if (!slot_active(g, mask, slot)) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T2* b0 = reinterpret_cast<T2*>(smem_raw);
     const int M = g.M, N = g.N, rows = g.rows;
@@ -126,7 +126,7 @@ k_x_inverse(GridDesc g, unsigned mask, const typename Cplx<R>::T* __restrict__ s
             double* __restrict__ partial) {
     using T2 = typename Cplx<R>::T;
     const int slot = blockIdx.y;
-    if (!((mask >> slot) & 1u)) return;
+    if (!slot_active(g, mask, slot)) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T2* b0 = reinterpret_cast<T2*>(smem_raw);
     const int M = g.M, N = g.N, rows = g.rows;
@@ -161,41 +161,39 @@ k_x_inverse(GridDesc g, unsigned mask, const typename Cplx<R>::T* __restrict__ s
 
     const long long fbase = (long long)slot * 3 * g.N3 + row0 * N;   // element offset of the tile
     T2* out = reinterpret_cast<T2*>(tau + fbase);
+    // output step: add r (correction sweeps), read the old field for the residual,
+    // or (XI_DIFF) write d = new - old to d32 and r32_out without touching tau
+    constexpr bool kRes = MODE == XI_INPLACE_RES || MODE == XI_ADD_R_RES;
+    constexpr bool kAddR = MODE == XI_ADD_R_RES || MODE == XI_ADD_R;
+    const bool resid = kRes && (g.dflags ? g.resid != 0 : true);
+    const bool addr = kAddR && (g.dflags ? (g.dflags[slot] & SF_ADDR) != 0 : true);
     double acc = 0.0;
     for (int q = threadIdx.x; q < rows * M; q += blockDim.x) {
         T2 v = res[q];
-        if (MODE == XI_PLAIN || MODE == XI_INPLACE) {
-            out[q] = v;
-        } else if (MODE == XI_INPLACE_RES) {
-            const T2 o = out[q];
-            const double da = (double)v.x - (double)o.x, db = (double)v.y - (double)o.y;
-            acc += da * da + db * db;
-            out[q] = v;
-        } else if (MODE == XI_ADD_R) {
-            const float2 rv = reinterpret_cast<const float2*>(r32 + fbase)[q];
-            v.x += R(rv.x);
-            v.y += R(rv.y);
-            out[q] = v;
-        } else if (MODE == XI_ADD_R_RES) {
-            const float2 rv = reinterpret_cast<const float2*>(r32 + fbase)[q];
-            v.x += R(rv.x);
-            v.y += R(rv.y);
-            const T2 o = out[q];
-            const double da = (double)v.x - (double)o.x, db = (double)v.y - (double)o.y;
-            acc += da * da + db * db;
-            out[q] = v;
-        } else {  // XI_DIFF: d = new - old, tau untouched
+        if (MODE == XI_DIFF) {
             const T2 o = out[q];
             const double da = (double)v.x - (double)o.x, db = (double)v.y - (double)o.y;
             acc += da * da + db * db;
             const float2 df = make_float2((float)da, (float)db);
             reinterpret_cast<float2*>(r32_out + fbase)[q] = df;
             reinterpret_cast<float2*>(d32 + fbase)[q] = df;
+            continue;
         }
+        if (addr) {
+            const float2 rv = reinterpret_cast<const float2*>(r32 + fbase)[q];
+            v.x += R(rv.x);
+            v.y += R(rv.y);
+        }
+        if (resid) {
+            const T2 o = out[q];
+            const double da = (double)v.x - (double)o.x, db = (double)v.y - (double)o.y;
+            acc += da * da + db * db;
+        }
+        out[q] = v;
     }
-    if (MODE == XI_INPLACE_RES || MODE == XI_ADD_R_RES || MODE == XI_DIFF) {
+    if (kRes || MODE == XI_DIFF) {   // uniform across the CTA
         double s = block_sum(acc, red);
-        if (threadIdx.x == 0) partial[(long long)slot * gridDim.x + blockIdx.x] = s;
+        if (threadIdx.x == 0 && (resid || MODE == XI_DIFF)) partial[(long long)slot * gridDim.x + blockIdx.x] = s;
     }
 }
 
@@ -208,7 +206,7 @@ __global__ void __launch_bounds__(kThreads)
 k_y_pass(GridDesc g, unsigned mask, typename Cplx<R>::T* __restrict__ spec) {
     using T2 = typename Cplx<R>::T;
     const int slot = blockIdx.y;
-    if (!((mask >> slot) & 1u)) return;
+    if (!slot_active(g, mask, slot)) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int N = g.N, M = g.M, P = g.Py;
     T2* b0 = reinterpret_cast<T2*>(smem_raw);
@@ -240,7 +238,7 @@ __global__ void __launch_bounds__(kThreads)
 k_z_pass(GridDesc g, unsigned mask, typename Cplx<R>::T* __restrict__ spec, double* __restrict__ partial) {
     using T2 = typename Cplx<R>::T;
     const int slot = blockIdx.y;
-    if (!((mask >> slot) & 1u)) return;
+    if (!slot_active(g, mask, slot)) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int N = g.N, M = g.M, P = g.Pz, P3 = 3 * P;
     T2* b0 = reinterpret_cast<T2*>(smem_raw);
@@ -262,6 +260,7 @@ k_z_pass(GridDesc g, unsigned mask, typename Cplx<R>::T* __restrict__ spec, doub
     T2* other = (res == b0) ? b1 : b0;
 
     if (MODE == Z_ITER || MODE == Z_ITER_NOB || MODE == Z_EQ) {
+        const bool addb = g.dflags ? (g.dflags[slot] & SF_ADDB) != 0 : MODE == Z_ITER;
         const R scale = R(1.0 / (double)g.N3);
         const R twok0E[3] = {R(2.0 * g.k0 * g.E[slot][0]), R(2.0 * g.k0 * g.E[slot][1]),
                              R(2.0 * g.k0 * g.E[slot][2])};
@@ -275,7 +274,7 @@ k_z_pass(GridDesc g, unsigned mask, typename Cplx<R>::T* __restrict__ spec, doub
             if (MODE == Z_EQ) {
                 acc += eq_mode(kx, ky, kz, N, s0, s1, s2);
             } else {
-                green_mode<R>(kx, ky, kz, N, scale, MODE == Z_ITER, twok0E, s0, s1, s2);
+                green_mode<R>(kx, ky, kz, N, scale, addb, twok0E, s0, s1, s2);
                 e[0] = s0;
                 e[P] = s1;
                 e[2 * P] = s2;
@@ -317,7 +316,7 @@ __global__ void k_reduce(const double* __restrict__ partial, int count, int grou
 template <typename R>
 __global__ void k_init_tau(GridDesc g, unsigned mask, R* __restrict__ tau) {
     const int slot = blockIdx.y;
-    if (!((mask >> slot) & 1u)) return;
+    if (!slot_active(g, mask, slot)) return;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < g.N3; i += (long long)gridDim.x * blockDim.x) {
         const int ph = g.phase[i];
         const double kp = ph == 0 ? g.KP[0] : (ph == 1 ? g.KP[1] : g.KP[2]);
@@ -345,7 +344,7 @@ __global__ void k_tau_to_e(GridDesc g, int slot, const R* __restrict__ tau, doub
 
 __global__ void k_widen(GridDesc g, unsigned mask, const float* __restrict__ src, double* __restrict__ dst) {
     const int slot = blockIdx.y;
-    if (!((mask >> slot) & 1u)) return;
+    if (!slot_active(g, mask, slot)) return;
     const long long n = 3 * g.N3, off = (long long)slot * n;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
         dst[off + i] = (double)src[off + i];
@@ -353,7 +352,7 @@ __global__ void k_widen(GridDesc g, unsigned mask, const float* __restrict__ src
 
 __global__ void k_axpy(GridDesc g, unsigned mask, const float* __restrict__ d, double* __restrict__ tau) {
     const int slot = blockIdx.y;
-    if (!((mask >> slot) & 1u)) return;
+    if (!slot_active(g, mask, slot)) return;
     const long long n = 3 * g.N3, off = (long long)slot * n;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
         tau[off + i] += (double)d[off + i];

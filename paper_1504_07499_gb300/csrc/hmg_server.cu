@@ -2,9 +2,12 @@
 // runs queued requests.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <chrono>
 #include <cstring>
+#include <memory>
 
+#include "hmg_engine.h"
 #include "hmg_runtime.h"
 #include "hmg_server.h"
 
@@ -51,6 +54,7 @@ hmg_status Server::submit(const uint8_t* phase, int N, const double k[3], double
     }
     r.ticket = next++;
     *ticket = r.ticket;
+    ++n_submitted;
     queue.push_back(r.ticket);
     reqs.emplace(r.ticket, std::move(r));
     cv.notify_all();
@@ -72,33 +76,125 @@ hmg_status Server::poll(uint64_t ticket, double K[9], hmg_info* info) {
     return s;
 }
 
+// Continuous batching: every engine tick advances all admitted FP32-bulk requests
+// together; between ticks, finished requests retire (their device state is freed)
+// and queued ones are admitted while their footprint fits the context budget.
+// FP64 requests run one at a time with the plain method.
+void Server::stats(long long out[6]) {
+    std::lock_guard<std::mutex> lk(mu);
+    out[0] = n_submitted;
+    out[1] = n_completed;
+    out[2] = max_resident;
+    out[3] = n_ticks;
+    out[4] = n_captures;
+    out[5] = n_launches;
+}
+
 void Server::loop() {
     hmg_ctx* ctx = nullptr;
     hmg_status cs = hmg_create(&ctx, device, budget);
+    std::unique_ptr<Engine> eng;
+    if (cs == HMG_OK) {
+        cudaSetDevice(device);
+        eng = std::make_unique<Engine>(ctx, ctx->stream, true);
+    }
+    std::map<Entry*, uint64_t> running;
     for (;;) {
-        uint64_t t;
-        Request* r;
+        std::vector<uint64_t> admit, fp64;
         {
             std::unique_lock<std::mutex> lk(mu);
-            cv.wait(lk, [this] { return stop || !queue.empty(); });
+            cv.wait(lk, [&] { return stop || !queue.empty() || !running.empty(); });
             if (stop) break;
-            t = queue.front();
-            queue.pop_front();
-            r = &reqs[t];
-            r->t_start = now_s();
+            size_t used = eng ? eng->bytes_in_use() : 0;
+            while (!queue.empty()) {
+                Request& r = reqs[queue.front()];
+                if (r.prec == HMG_FP64) {
+                    if (!running.empty() || !fp64.empty()) break;   // plain FP64 runs alone
+                    fp64.push_back(r.ticket);
+                    queue.pop_front();
+                    break;
+                }
+                const size_t need = state_bytes(r.N, false, 3);
+                if ((int)running.size() + (int)admit.size() >= max_slots) break;
+                // the first request of an idle loop is always admitted (it fits the budget
+                // by the check in hmg_submit); later ones while their footprint fits
+                if ((!running.empty() || !admit.empty()) && used + need > (size_t)(0.95 * (double)budget)) break;
+                used += need;
+                admit.push_back(r.ticket);
+                queue.pop_front();
+            }
+            for (uint64_t t : admit) reqs[t].t_start = now_s();
+            for (uint64_t t : fp64) reqs[t].t_start = now_s();
         }
-        double K[9] = {0};
-        hmg_info info{};
-        hmg_status s = cs != HMG_OK ? cs
-                                    : hmg_solve(ctx, r->phase.data(), r->N, r->k[0], r->k[1], r->k[2], r->tol, r->prec,
-                                                0, K, &info);
-        std::lock_guard<std::mutex> lk(mu);
-        r->status = s == HMG_PENDING ? HMG_CUDA_ERROR : s;
-        memcpy(r->K, K, sizeof(K));
-        r->info = info;
-        r->t_done = now_s();
-        r->info.seconds = r->t_done - r->t_submit;
+        for (uint64_t t : fp64) {
+            Request* r;
+            {
+                std::lock_guard<std::mutex> lk(mu);
+                r = &reqs[t];
+            }
+            double K[9] = {0};
+            hmg_info info{};
+            hmg_status s = cs != HMG_OK ? cs
+                                        : hmg_solve(ctx, r->phase.data(), r->N, r->k[0], r->k[1], r->k[2], r->tol,
+                                                    HMG_FP64, 0, K, &info);
+            std::lock_guard<std::mutex> lk(mu);
+            r->status = s == HMG_PENDING ? HMG_CUDA_ERROR : s;
+            memcpy(r->K, K, sizeof(K));
+            r->info = info;
+            r->t_done = now_s();
+            r->info.seconds = r->t_done - r->t_submit;
+            ++n_completed;
+        }
+        for (uint64_t t : admit) {
+            Request* r;
+            {
+                std::lock_guard<std::mutex> lk(mu);
+                r = &reqs[t];
+            }
+            Entry* e = nullptr;
+            hmg_status s = cs != HMG_OK ? cs : eng->add((long long)t, r->phase.data(), r->N, r->k, r->tol, 0, &e);
+            if (s != HMG_OK) {
+                std::lock_guard<std::mutex> lk(mu);
+                r->status = s;
+                r->t_done = now_s();
+                continue;
+            }
+            running[e] = t;
+        }
+        if (running.empty()) continue;
+        {
+            std::lock_guard<std::mutex> lk(mu);
+            max_resident = std::max(max_resident, (long long)running.size());
+        }
+        hmg_status s = eng->tick();
+        {
+            std::lock_guard<std::mutex> lk(mu);
+            ++n_ticks;
+            n_captures = eng->graph_captures;
+            n_launches = eng->graph_launches;
+        }
+        std::vector<Entry*> done;
+        for (auto& kv : running)
+            if (kv.first->finished || s != HMG_OK) done.push_back(kv.first);
+        for (Entry* e : done) {
+            const uint64_t t = running[e];
+            {
+                std::lock_guard<std::mutex> lk(mu);
+                Request& r = reqs[t];
+                r.status = e->finished ? e->result : s;
+                memcpy(r.K, e->K, sizeof(r.K));
+                r.info = e->info;
+                r.t_done = now_s();
+                r.info.seconds = r.t_done - r.t_submit;
+                r.phase.clear();
+                r.phase.shrink_to_fit();
+                ++n_completed;
+            }
+            running.erase(e);
+            eng->remove(e);
+        }
     }
+    eng.reset();
     if (ctx) hmg_destroy(ctx);
 }
 
@@ -125,6 +221,17 @@ hmg_status hmg_submit(hmg_ctx* ctx, const uint8_t* phase, int N, double km, doub
     return ctx->server->submit(phase, N, k, tol, precision, ticket);
 }
 
+hmg_status hmg_server_stats(hmg_ctx* ctx, long long out[6]) {
+    g_last_error.clear();
+    if (!ctx || !out) {
+        set_error("bad arguments");
+        return HMG_INVALID_ARG;
+    }
+    for (int i = 0; i < 6; ++i) out[i] = 0;
+    if (ctx->server) ctx->server->stats(out);
+    return HMG_OK;
+}
+
 hmg_status hmg_poll(hmg_ctx* ctx, uint64_t ticket, double K_out[9], hmg_info* info) {
     g_last_error.clear();
     if (!ctx || !K_out) {
@@ -142,16 +249,57 @@ hmg_status hmg_solve_batch(hmg_ctx* ctx, int count, const uint8_t* const* phases
                            const double* k3, double tol, hmg_precision precision, int max_iter, double* K_out,
                            hmg_info* info) {
     g_last_error.clear();
-    if (!ctx || count < 1 || !phases || !N_list || !k3 || !K_out) {
+    if (!ctx || count < 1 || !phases || !N_list || !k3 || !K_out || !(tol > 0) ||
+        (precision != HMG_FP64 && precision != HMG_FP32_BULK)) {
         set_error("bad batch arguments");
         return HMG_INVALID_ARG;
     }
+    for (int i = 0; i < count; ++i)
+        if (!phases[i] || !valid_N(N_list[i]) || !(k3[3 * i] > 0 && k3[3 * i + 1] > 0 && k3[3 * i + 2] > 0)) {
+            set_error("batch entry %d: bad phase pointer, N or conductivity", i);
+            return HMG_INVALID_ARG;
+        }
     hmg_status worst = HMG_OK;
-    for (int i = 0; i < count; ++i) {
-        hmg_status s = hmg_solve(ctx, phases[i], N_list[i], k3[3 * i], k3[3 * i + 1], k3[3 * i + 2], tol, precision,
-                                 max_iter, K_out + 9 * i, info ? info + i : nullptr);
-        if (s == HMG_INVALID_ARG || s == HMG_CUDA_ERROR || s == HMG_OUT_OF_MEMORY) return s;
-        if (s != HMG_OK && worst == HMG_OK) worst = s;
+    if (precision == HMG_FP64) {   // the plain method, one RVE after the other
+        for (int i = 0; i < count; ++i) {
+            hmg_status s = hmg_solve(ctx, phases[i], N_list[i], k3[3 * i], k3[3 * i + 1], k3[3 * i + 2], tol,
+                                     precision, max_iter, K_out + 9 * i, info ? info + i : nullptr);
+            if (s == HMG_INVALID_ARG || s == HMG_CUDA_ERROR || s == HMG_OUT_OF_MEMORY) return s;
+            if (s != HMG_OK && worst == HMG_OK) worst = s;
+        }
+        return worst;
+    }
+    cudaSetDevice(ctx->device);
+    auto t0 = now_s();
+    ctx->solve.free_all(ctx);   // the engine holds its own per-RVE state
+    Engine eng(ctx, ctx->stream, true);
+    int next = 0;
+    std::map<Entry*, int> live;
+    while (next < count || !live.empty()) {
+        // admit as many RVEs as fit the budget (waves when the batch is larger)
+        while (next < count) {
+            Entry* e = nullptr;
+            hmg_status s = eng.add(next, phases[next], N_list[next], k3 + 3 * next, tol, max_iter, &e);
+            if (s == HMG_OUT_OF_MEMORY && !live.empty()) break;
+            if (s != HMG_OK) return s;
+            live[e] = next++;
+        }
+        hmg_status s = eng.tick();
+        if (s != HMG_OK) return s;
+        std::vector<Entry*> done;
+        for (auto& kv : live)
+            if (kv.first->finished) done.push_back(kv.first);
+        for (Entry* e : done) {
+            const int i = live[e];
+            memcpy(K_out + 9 * i, e->K, 9 * sizeof(double));
+            if (info) {
+                info[i] = e->info;
+                info[i].seconds = now_s() - t0;
+            }
+            if (e->result != HMG_OK && worst == HMG_OK) worst = e->result;
+            live.erase(e);
+            eng.remove(e);
+        }
     }
     return worst;
 }

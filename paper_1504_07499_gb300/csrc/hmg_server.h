@@ -23,6 +23,7 @@ struct Request {
     double K[9] = {0};
     hmg_info info{};
     double t_submit = 0, t_start = 0, t_done = 0;
+    bool admitted = false;
 };
 
 struct Server {
@@ -30,11 +31,15 @@ struct Server {
     ~Server();
     hmg_status submit(const uint8_t* phase, int N, const double k[3], double tol, hmg_precision p, uint64_t* ticket);
     hmg_status poll(uint64_t ticket, double K[9], hmg_info* info);
+    // counters: submitted, completed, most requests resident at once, engine ticks,
+    // graph captures, graph launches
+    void stats(long long out[6]);
 
    private:
     void loop();
     int device;
     size_t budget;
+    int max_slots = 64;
     std::mutex mu;
     std::condition_variable cv;
     std::deque<uint64_t> queue;
@@ -42,6 +47,7 @@ struct Server {
     uint64_t next = 1;
     bool stop = false;
     std::thread worker;
+    long long n_submitted = 0, n_completed = 0, max_resident = 0, n_ticks = 0, n_captures = 0, n_launches = 0;
 };
 
 }  // namespace hmg

@@ -29,7 +29,8 @@ STATUS_NAMES = {0: "OK", 1: "PENDING", -1: "INVALID_ARG", -2: "OUT_OF_MEMORY", -
 EXPORTS = ["hmg_version", "hmg_last_error", "hmg_create", "hmg_destroy", "hmg_voxelize", "hmg_solve",
            "hmg_solve_fields", "hmg_em_iterate", "hmg_equilibrium", "hmg_fft_forward", "hmg_fft_inverse",
            "hmg_solve_batch", "hmg_submit", "hmg_poll", "hmg_footprint", "hmg_trace_enable",
-           "hmg_trace_read", "hmg_equilibrium_noalloc", "hmg_set_variant", "hmg_get_variant"]
+           "hmg_trace_read", "hmg_equilibrium_noalloc", "hmg_set_variant", "hmg_get_variant",
+           "hmg_server_stats"]
 HMG_NOALLOC_MAX_N = 64
 KERNEL_KINDS = ["x_forward", "y_forward", "z_green", "y_inverse", "x_inverse", "eq_x", "eq_z", "other"]
 
@@ -82,6 +83,7 @@ def lib() -> C.CDLL:
         L.hmg_submit.argtypes = [vp, vp, i, d, d, d, d, i, C.POINTER(C.c_uint64)]
         L.hmg_poll.argtypes = [vp, C.c_uint64, dp, C.POINTER(hmg_info)]
         L.hmg_equilibrium_noalloc.argtypes = [vp, i, d, d, d, vp, dp, dp]
+        L.hmg_server_stats.argtypes = [vp, C.POINTER(C.c_longlong)]
         L.hmg_set_variant.argtypes = [vp, i, i]
         L.hmg_get_variant.argtypes = [vp, i, C.POINTER(C.c_int)]
         L.hmg_trace_enable.argtypes = [vp, i]
@@ -228,6 +230,13 @@ def hmg_poll(ctx: int, ticket: int):
         return st, None, None
     _check(st, (HMG_OK, HMG_NOT_CONVERGED, HMG_DIVERGED))
     return st, K.reshape(3, 3), info.as_dict()
+
+
+def hmg_server_stats(ctx: int) -> dict:
+    out = (C.c_longlong * 6)()
+    _check(lib().hmg_server_stats(ctx, out))
+    keys = ["submitted", "completed", "max_resident", "ticks", "graph_captures", "graph_launches"]
+    return dict(zip(keys, [int(v) for v in out]))
 
 
 def hmg_set_variant(ctx: int, N: int, variant: int) -> None:
