@@ -166,11 +166,21 @@ def main() -> None:
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison solve")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--mode", default="single", choices=["single", "batch", "serve"],
+                    help="single: the 256^3 RVE (default); batch: 64 mixed-size RVEs in one engine; "
+                         "serve: Poisson request stream through hmg_submit/hmg_poll")
+    ap.add_argument("--requests", type=int, default=48, help="serve mode: requests per arrival rate")
     ap.add_argument("--sweeps-only", type=int, default=0,
                     help="profiling case: voxelize, run this many sweeps of one gradient, exit")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.mode == "batch":
+        run_batch(args)
+        return
+    if args.mode == "serve":
+        run_serve(args)
         return
 
     import torch
@@ -345,6 +355,183 @@ def main() -> None:
         dist.barrier()
         dist.destroy_process_group()
     ctx.close()
+
+
+# ---------------------------------------------------------------------------
+# many RVEs: batched solves and the request loop
+# ---------------------------------------------------------------------------
+
+def _spheres(args_tuple):
+    from paper_1504_07499_gb300 import inputs as I
+    seed, n, f = args_tuple
+    return I.generate_spheres(seed, n, f).spheres
+
+
+def _sphere_lists(specs):
+    """Seeded sphere lists generated in parallel (spawned workers, before CUDA starts)."""
+    import multiprocessing as mp
+    with mp.get_context("spawn").Pool(min(len(specs), os.cpu_count() or 1)) as pool:
+        return pool.map(_spheres, specs)
+
+
+def run_batch(args) -> None:
+    """Stochastic averaging batch: 64 RVEs (24 x 64^3, 24 x 96^3, 16 x 128^3), n ~ U{10..100},
+    f ~ U[0.10, 0.40], l ~ U[0.1, 0.5], k 0.20/0.25/400, solved by hmg_solve_batch (every
+    engine tick is one CUDA-graph launch over all RVEs); compared with the same RVEs solved
+    one after the other (FP32 bulk) and with the plain FP64 method on a subset."""
+    from paper_1504_07499_gb300 import inputs as I
+    rec = I.batch_recipe()
+    lists = _sphere_lists([(r["seed"], r["n"], r["f"]) for r in rec])
+    import torch
+    from paper_1504_07499_gb300 import build, hmg
+    build.build()
+    ctx = hmg.Context(0)
+    phases, Ns = [], []
+    for r, sph in zip(rec, lists):
+        ph = torch.empty(r["N"] ** 3, dtype=torch.uint8, device="cuda")
+        hmg.hmg_voxelize(ctx.handle, sph, r["layer"], r["N"], ph)
+        phases.append(ph)
+        Ns.append(r["N"])
+    k3 = np.tile(np.array(K_PHASES), (len(rec), 1))
+    torch.cuda.synchronize()
+    for _ in range(args.warmup):
+        hmg.hmg_solve_batch(ctx.handle, phases, Ns, k3, TOL, hmg.HMG_FP32_BULK)
+    t = time.perf_counter()
+    vox = 0
+    for _ in range(args.steps):
+        K, infos, st = hmg.hmg_solve_batch(ctx.handle, phases, Ns, k3, TOL, hmg.HMG_FP32_BULK)
+        vox += sum(N ** 3 * sum(i["iters"]) for N, i in zip(Ns, infos))
+    dt = (time.perf_counter() - t) / args.steps
+    # one after the other, same engine arithmetic per RVE
+    t = time.perf_counter()
+    vox_seq = 0
+    for ph, N in zip(phases, Ns):
+        _, info, _ = hmg.hmg_solve(ctx.handle, ph, N, K_PHASES, TOL, hmg.HMG_FP32_BULK)
+        vox_seq += N ** 3 * sum(info["iters"])
+    dt_seq = time.perf_counter() - t
+    # plain FP64 on the first RVE of each size
+    fp64 = {}
+    for N in sorted(set(Ns)):
+        i = Ns.index(N)
+        t = time.perf_counter()
+        _, info, _ = hmg.hmg_solve(ctx.handle, phases[i], N, K_PHASES, TOL, hmg.HMG_FP64)
+        fp64[N] = {"solve_s": time.perf_counter() - t, "voxel_iter_per_s": N ** 3 * sum(info["iters"]) /
+                   (time.perf_counter() - t)}
+    est_fp64_s = sum(fp64[N]["solve_s"] for N in Ns)
+    kbar = {}
+    for N in sorted(set(Ns)):
+        d = np.array([np.trace(K[i]) / 3 for i in range(len(Ns)) if Ns[i] == N])
+        kbar[str(N)] = {"mean": float(d.mean()), "std": float(d.std(ddof=1)), "count": int(d.size)}
+    line = {"metric": "voxel-iterations/s, 64 mixed-size RVEs in one engine (3 unit gradients, tol 1e-8)",
+            "value": vox / args.steps / dt, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * dt, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "batch64: 24 x 64^3, 24 x 96^3, 16 x 128^3 RVEs (seeds 4000-4063), "
+                                   "n ~ U{10..100}, f ~ U[0.10,0.40], l ~ U[0.1,0.5], k 0.20/0.25/400",
+                       "precision": "fp32bulk", "total_voxels": int(sum(N ** 3 for N in Ns))},
+            "solves_per_s": len(Ns) / dt,
+            "sequential_fp32bulk": {"voxel_iter_per_s": vox_seq / dt_seq, "seconds": dt_seq,
+                                    "batch_speedup": dt_seq / dt},
+            "plain_fp64_estimate": {"seconds": est_fp64_s, "per_size": fp64, "batch_speedup": est_fp64_s / dt},
+            "mean_K_trace_over_3": kbar,
+            "status_all_ok": bool(st == hmg.HMG_OK)}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+
+
+def run_serve(args) -> None:
+    """Poisson stream of requests (seed 5000): N uniform over {64, 96, 128, 192, 256},
+    k_coat over {40, 400, 4000}, 100 spheres at 40 %, l in {0.1, 0.3, 0.5}, FP32 bulk,
+    through hmg_submit / hmg_poll at 0.5x, 1x and 1.5x the rate sequential FP32-bulk
+    solves sustain.  Sequential FP32-bulk and plain-FP64 service of the same arrivals is
+    simulated from measured per-request service times (FIFO, one at a time)."""
+    from paper_1504_07499_gb300 import inputs as I
+    pool_specs = [(5000 + i, 100, 0.40) for i in range(4)]
+    lists = _sphere_lists(pool_specs)
+    import torch
+    from paper_1504_07499_gb300 import build, hmg
+    build.build()
+    u = I.SplitMix64(5000, 17).uniform(4 * args.requests).reshape(args.requests, 4)
+    sizes, kcs, layers = (64, 96, 128, 192, 256), (40.0, 400.0, 4000.0), (0.1, 0.3, 0.5)
+    reqs = [(sizes[int(a * 5)], kcs[int(b * 3)], layers[int(c * 3)], int(d * 4)) for a, b, c, d in u]
+    ctx = hmg.Context(0)
+    phase_cache = {}
+    for N, kc, layer, li in reqs:
+        key = (N, layer, li)
+        if key not in phase_cache:
+            ph = np.empty(N ** 3, dtype=np.uint8)
+            hmg.hmg_voxelize(ctx.handle, lists[li], layer, N, ph)
+            phase_cache[key] = ph
+    # service times of sequential solves (FP32 bulk; plain FP64 per (N, k_coat) class)
+    svc32, svc64 = [], {}
+    for N, kc, layer, li in reqs:
+        t = time.perf_counter()
+        hmg.hmg_solve(ctx.handle, phase_cache[(N, layer, li)], N, (0.20, 0.25, kc), TOL, hmg.HMG_FP32_BULK)
+        svc32.append(time.perf_counter() - t)
+    for N, kc, layer, li in reqs:
+        if (N, kc) not in svc64 and N <= 128:
+            t = time.perf_counter()
+            hmg.hmg_solve(ctx.handle, phase_cache[(N, layer, li)], N, (0.20, 0.25, kc), TOL, hmg.HMG_FP64)
+            svc64[(N, kc)] = time.perf_counter() - t
+    ctx.close()
+    # larger classes: scale the measured FP64 time of the same contrast by the voxel count
+    def fp64_time(N, kc):
+        if (N, kc) in svc64:
+            return svc64[(N, kc)]
+        base = max((n for (n, k) in svc64 if k == kc), default=None)
+        return svc64[(base, kc)] * (N / base) ** 3 * np.log2(N) / np.log2(base)
+
+    def fifo(arrivals, service):
+        done, lat = 0.0, []
+        for a, s in zip(arrivals, service):
+            done = max(done, a) + s
+            lat.append(done - a)
+        return done, lat
+
+    mean32 = float(np.mean(svc32))
+    results = []
+    for factor in (0.5, 1.0, 1.5):
+        rate = factor / mean32
+        arr = I.poisson_arrivals(5000, rate, len(reqs))
+        c = hmg.Context(0)
+        tickets, t0 = [], time.perf_counter()
+        for (N, kc, layer, li), a in zip(reqs, arr):
+            while time.perf_counter() - t0 < a:
+                time.sleep(0.0005)
+            tickets.append(hmg.hmg_submit(c.handle, phase_cache[(N, layer, li)], N, (0.20, 0.25, kc), TOL,
+                                          hmg.HMG_FP32_BULK))
+        lat, pending = [], set(tickets)
+        while pending:
+            for t in list(pending):
+                st, K, info = hmg.hmg_poll(c.handle, t)
+                if st != hmg.HMG_PENDING:
+                    lat.append(info["seconds"])
+                    pending.discard(t)
+            time.sleep(0.002)
+        makespan = time.perf_counter() - t0
+        stats = hmg.hmg_server_stats(c.handle)
+        c.close()
+        end32, lat32 = fifo(arr, svc32)
+        end64, lat64 = fifo(arr, [fp64_time(N, kc) for N, kc, _, _ in reqs])
+        results.append({"rate_factor": factor, "rate_hz": rate, "solves_per_s": len(reqs) / makespan,
+                        "p50_ms": 1e3 * float(np.percentile(lat, 50)), "p99_ms": 1e3 * float(np.percentile(lat, 99)),
+                        "max_resident": stats["max_resident"], "graph_launches": stats["graph_launches"],
+                        "sequential_fp32bulk": {"solves_per_s": len(reqs) / end32,
+                                                "p50_ms": 1e3 * float(np.percentile(lat32, 50)),
+                                                "p99_ms": 1e3 * float(np.percentile(lat32, 99))},
+                        "sequential_fp64": {"solves_per_s": len(reqs) / end64,
+                                            "p50_ms": 1e3 * float(np.percentile(lat64, 50)),
+                                            "p99_ms": 1e3 * float(np.percentile(lat64, 99))}})
+    line = {"metric": "solves/s and p50/p99 latency of a Poisson request stream (serving)",
+            "value": results[-1]["solves_per_s"], "unit": "solves/s", "n_gpus": 1, "steps": len(reqs),
+            "warmup": 0, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "serve: N in {64,96,128,192,256}, k_coat in {40,400,4000}, 100 spheres at 40%, "
+                                   "l in {0.1,0.3,0.5}, Poisson arrivals seed 5000", "requests": len(reqs),
+                       "mean_sequential_fp32bulk_service_s": mean32,
+                       "fp64_service_measured": {f"{k[0]}/{k[1]}": v for k, v in svc64.items()}},
+            "rates": results}
+    print(json.dumps(line), flush=True)
 
 
 def _kernel_sha() -> str:
