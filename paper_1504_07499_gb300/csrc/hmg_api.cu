@@ -224,7 +224,7 @@ size_t state_bytes(int N, bool fp64, int nslots) {
     const size_t field32 = (size_t)nslots * 3 * N3 * 4;
     size_t b = N3 + 2 * field64;                        // phase, tau64, spec64
     if (!fp64) b += 3 * field32;                        // f32, r32, spec32
-    b += (size_t)nslots * 2 * 4 * (3 * (size_t)N * N) * 8 + 4096;   // partials
+    b += (size_t)nslots * 3 * 4 * (3 * (size_t)N * N) * 8 + 4096;   // partials
     return b;
 }
 
@@ -248,8 +248,10 @@ bool SolveState::ensure(Context* c, int N_, bool fp64_, int nslots_) {
     const size_t np = (size_t)nslots * 4 * 3 * N * N + 64;
     partial = (double*)c->alloc(np * sizeof(double));
     partial2 = (double*)c->alloc(np * sizeof(double));
+    partial3 = (double*)c->alloc(np * sizeof(double));
     red = (double*)c->alloc(64 * sizeof(double));
-    bool ok = phase && tau64 && spec64 && partial && partial2 && red && (fp64 || (f32buf && r32 && spec32));
+    bool ok = phase && tau64 && spec64 && partial && partial2 && partial3 && red &&
+              (fp64 || (f32buf && r32 && spec32));
     if (!ok) {
         free_all(c);
         return false;
@@ -259,7 +261,7 @@ bool SolveState::ensure(Context* c, int N_, bool fp64_, int nslots_) {
 
 void SolveState::free_all(Context* c) {
     for (void** p : {(void**)&phase, (void**)&tau64, &spec64, (void**)&f32buf, (void**)&r32, &spec32,
-                     (void**)&partial, (void**)&partial2, (void**)&red}) {
+                     (void**)&partial, (void**)&partial2, (void**)&partial3, (void**)&red}) {
         c->release(*p);
         *p = nullptr;
     }
@@ -370,19 +372,19 @@ void Solver::sweep(unsigned mask, R* field, void* spec, int zmode, int ximode, c
     if (ximode == XI_ADD_R_RES) xb += f * F + f * 4;            // old field and r
     if (ximode == XI_ADD_R) xb += f * 4;                         // r
     if (ximode == XI_DIFF) xb = f * F + f * F + 2 * f * 4;      // spectrum, old field, d and r out
-    HMG_TRACED(HMG_K_X_INVERSE, xb,
-               launch_x_inverse<R>(g, ximode, mask, spec, field, r32in, d32, r32out, s->partial, st));
+    double* pb = psweep ? psweep : s->partial;
+    HMG_TRACED(HMG_K_X_INVERSE, xb, launch_x_inverse<R>(g, ximode, mask, spec, field, r32in, d32, r32out, pb, st));
     if (ximode == XI_INPLACE_RES || ximode == XI_ADD_R_RES || ximode == XI_DIFF)
-        HMG_TRACED(HMG_K_OTHER, 0.0, launch_reduce(s->partial, g.nslots, x_ctas_for<R>(g), 1, s->red + red_off, st));
+        HMG_TRACED(HMG_K_OTHER, 0.0, launch_reduce(pb, g.nslots, x_ctas_for<R>(g), 1, s->red + red_off, st));
 }
 
 template <typename R>
 void Solver::equilibrium(unsigned mask, const R* field, void* spec) {
     const double f = (double)popc(mask) * 3.0 * (double)g.N3;
     const double F = sizeof(R);
-    HMG_TRACED(HMG_K_EQ_X, f * 2 * F + (double)g.N3,
-               launch_x_forward<R>(g, XF_FLUX, mask, field, spec, s->partial, st));
-    HMG_TRACED(HMG_K_OTHER, 0.0, launch_reduce(s->partial, g.nslots, x_ctas_for<R>(g), 3, s->red + 16, st));
+    double* pb = pflux ? pflux : s->partial;
+    HMG_TRACED(HMG_K_EQ_X, f * 2 * F + (double)g.N3, launch_x_forward<R>(g, XF_FLUX, mask, field, spec, pb, st));
+    HMG_TRACED(HMG_K_OTHER, 0.0, launch_reduce(pb, g.nslots, x_ctas_for<R>(g), 3, s->red + 16, st));
     HMG_TRACED(HMG_K_Y_FORWARD, f * 2 * F, launch_y_pass<R>(g, true, mask, spec, st));
     HMG_TRACED(HMG_K_EQ_Z, f * F, launch_z_pass<R>(g, Z_EQ, mask, spec, s->partial2, st));
     HMG_TRACED(HMG_K_OTHER, 0.0, launch_reduce(s->partial2, g.nslots, z_ctas_for<R>(g), 1, s->red + 32, st));
@@ -467,16 +469,21 @@ hmg_status Solver::run_fp64(int max_iter, double tol, hmg_info* info, double K[9
 }
 
 // FP32 bulk: FP32 sweeps until the FP32 residual stalls, then FP64 defect correction
-// rounds: r = T tau64 + b - tau64 (one FP64 sweep), FP32 sweeps on delta = T delta + r,
-// tau64 += delta, until the FP64 residuals meet the tolerance.
-hmg_status Solver::run_bulk(int max_iter, double tol, hmg_info* info, double K[9]) {
-    enum { PH_A = 0, PH_OUTER = 1, PH_INNER = 2, PH_DONE = 3 };
+// rounds: r = T tau64 + b - tau64 (one FP64 sweep), the FP64 equilibrium test when the
+// FP64 residual is below tol, FP32 sweeps on delta = T delta + r, tau64 += delta, until
+// the FP64 residuals meet the tolerance.  Each tick launches the FP64 work of the
+// gradients that need it on a second stream, next to a block of FP32 sweeps of the
+// others (FP64 arithmetic and HBM traffic overlap); the FP64 equilibrium test of a
+// gradient runs in the tick after its FP64 sweep.  Each gradient goes through the
+// same sequence of operations whatever the others do.
+hmg_status Solver::run_bulk(int max_iter, double tol, hmg_info* info, double K[9], cudaStream_t st64) {
+    enum { PH_A = 0, PH_OUTER = 1, PH_EQ = 2, PH_INNER = 3, PH_DONE = 4 };
     const unsigned all = (1u << g.nslots) - 1u;
     HMG_TRACED(HMG_K_OTHER, 0.0, launch_init_tau<float>(g, all, s->f32buf, st));
     int state[3], iters[3] = {0, 0, 0}, it64[3] = {0, 0, 0}, status[3];
     double eps_comp[3] = {INFINITY, INFINITY, INFINITY}, eps_eq[3] = {INFINITY, INFINITY, INFINITY};
     double eps32[3] = {INFINITY, INFINITY, INFINITY}, best[3], outer_eps[3] = {INFINITY, INFINITY, INFINITY};
-    int since_best[3] = {0, 0, 0}, inner_n[3] = {0, 0, 0};
+    int since_best[3] = {0, 0, 0};
     double flux[3][3] = {};
     int rounds = 0;
     for (int sl = 0; sl < 3; ++sl) {
@@ -493,65 +500,89 @@ hmg_status Solver::run_bulk(int max_iter, double tol, hmg_info* info, double K[9
             if (state[sl] == ph) m |= 1u << sl;
         return m;
     };
+    Solver s64{g, s, st64, tr, s->partial3, s->partial3};
+    cudaEvent_t ready;
+    if (cudaEventCreateWithFlags(&ready, cudaEventDisableTiming) != cudaSuccess) {
+        set_error("event create failed");
+        return HMG_CUDA_ERROR;
+    }
+    double h[64];
     int total = 0;
-    while (mask_of(PH_DONE) != all) {
-        if (total >= max_iter) break;
+    hmg_status err = HMG_OK;
+    while (mask_of(PH_DONE) != all && total < max_iter) {
         ++total;
-        // FP64 outer sweep
-        unsigned mo = mask_of(PH_OUTER);
-        if (mo) {
-            sweep<double>(mo, s->tau64, s->spec64, Z_ITER, XI_DIFF, nullptr, s->f32buf, s->r32);
-            double h[3];
-            if (!fetch(h, 0, g.nslots)) return HMG_CUDA_ERROR;
-            unsigned eqm = 0;
-            for (int sl = 0; sl < g.nslots; ++sl) {
-                if (!((mo >> sl) & 1u)) continue;
-                ++iters[sl];
-                ++it64[sl];
-                eps_comp[sl] = eps_from_sum(h[sl], sl);
-                outer_eps[sl] = eps_comp[sl];
-                if (!std::isfinite(eps_comp[sl])) {
-                    status[sl] = HMG_DIVERGED;
-                    state[sl] = PH_DONE;
-                } else if (eps_comp[sl] < tol) {
-                    eqm |= 1u << sl;
-                }
-            }
-            if (eqm) {
-                if (!check_eq<double>(eqm, s->tau64, s->spec64, eps_eq, flux)) return HMG_CUDA_ERROR;
-                for (int sl = 0; sl < g.nslots; ++sl)
-                    if (((eqm >> sl) & 1u) && eps_eq[sl] < tol) {
-                        status[sl] = HMG_OK;
-                        state[sl] = PH_DONE;
-                    }
-            }
-            for (int sl = 0; sl < g.nslots; ++sl)
-                if (((mo >> sl) & 1u) && state[sl] == PH_OUTER) {
-                    state[sl] = PH_INNER;
-                    best[sl] = INFINITY;
-                    since_best[sl] = 0;
-                    inner_n[sl] = 0;
-                    ++rounds;
-                }
-            continue;
+        // FP64 work on the second stream, after this stream's pending transitions
+        const unsigned me = mask_of(PH_EQ), mo = mask_of(PH_OUTER);
+        if (me || mo) {
+            cudaEventRecord(ready, st);
+            cudaStreamWaitEvent(st64, ready, 0);
         }
-        // FP32 sweeps, plain (phase A) and defect-correction (inner), in blocks of
-        // `blk` sweeps: only the last sweep of a block reads the old field for the
-        // residual, and the host synchronizes once per block
-        unsigned ma = mask_of(PH_A), mi = mask_of(PH_INNER);
+        if (me) s64.equilibrium<double>(me, s->tau64, s->spec64);
+        if (mo) s64.sweep<double>(mo, s->tau64, s->spec64, Z_ITER, XI_DIFF, nullptr, s->f32buf, s->r32, 48);
+        if (me || mo) cudaMemcpyAsync(h + 16, s->red + 16, 40 * sizeof(double), cudaMemcpyDeviceToHost, st64);
+        // a block of FP32 sweeps: plain (phase A) and defect-correction (inner)
+        const unsigned ma = mask_of(PH_A), mi = mask_of(PH_INNER);
         const int blk = std::max(1, std::min(kResidualEvery, max_iter - total + 1));
-        for (int b = 0; b < blk; ++b) {
-            const bool last = b == blk - 1;
-            if (ma)
-                sweep<float>(ma, s->f32buf, s->spec32, Z_ITER, last ? XI_INPLACE_RES : XI_INPLACE, nullptr, nullptr,
-                             nullptr, 0);
-            if (mi)
-                sweep<float>(mi, s->f32buf, s->spec32, Z_ITER_NOB, last ? XI_ADD_R_RES : XI_ADD_R, s->r32, nullptr,
-                             nullptr, 8);
+        if (ma || mi) {
+            for (int b = 0; b < blk; ++b) {
+                const bool last = b == blk - 1;
+                if (ma)
+                    sweep<float>(ma, s->f32buf, s->spec32, Z_ITER, last ? XI_INPLACE_RES : XI_INPLACE, nullptr,
+                                 nullptr, nullptr, 0);
+                if (mi)
+                    sweep<float>(mi, s->f32buf, s->spec32, Z_ITER_NOB, last ? XI_ADD_R_RES : XI_ADD_R, s->r32,
+                                 nullptr, nullptr, 8);
+            }
+            cudaMemcpyAsync(h, s->red, 16 * sizeof(double), cudaMemcpyDeviceToHost, st);
+            total += blk - 1;
         }
-        total += blk - 1;
-        double h[16];
-        if (!fetch(h, 0, 16)) return HMG_CUDA_ERROR;
+        cudaError_t ce = cudaStreamSynchronize(st);
+        if (ce == cudaSuccess) ce = cudaStreamSynchronize(st64);
+        if (ce != cudaSuccess) {
+            set_error("CUDA error: %s", cudaGetErrorString(ce));
+            err = HMG_CUDA_ERROR;
+            break;
+        }
+        if (tr) tr->collect();
+        // equilibrium tests (step 1 in FP64)
+        for (int sl = 0; sl < g.nslots; ++sl) {
+            if (!((me >> sl) & 1u)) continue;
+            double nrm = 0.0;
+            for (int c = 0; c < 3; ++c) {
+                flux[sl][c] = h[16 + sl * 3 + c] / (double)g.N3;
+                nrm += flux[sl][c] * flux[sl][c];
+            }
+            eps_eq[sl] = std::sqrt(h[32 + sl]) / std::sqrt(nrm);
+            if (eps_eq[sl] < tol) {
+                status[sl] = HMG_OK;
+                state[sl] = PH_DONE;
+            } else {
+                state[sl] = PH_INNER;
+                best[sl] = INFINITY;
+                since_best[sl] = 0;
+                ++rounds;
+            }
+        }
+        // FP64 correction sweeps
+        for (int sl = 0; sl < g.nslots; ++sl) {
+            if (!((mo >> sl) & 1u)) continue;
+            ++iters[sl];
+            ++it64[sl];
+            eps_comp[sl] = eps_from_sum(h[48 + sl], sl);
+            outer_eps[sl] = eps_comp[sl];
+            if (!std::isfinite(eps_comp[sl])) {
+                status[sl] = HMG_DIVERGED;
+                state[sl] = PH_DONE;
+            } else if (eps_comp[sl] < tol) {
+                state[sl] = PH_EQ;
+            } else {
+                state[sl] = PH_INNER;
+                best[sl] = INFINITY;
+                since_best[sl] = 0;
+                ++rounds;
+            }
+        }
+        // FP32 blocks
         unsigned to_outer_a = 0, to_outer_i = 0;
         for (int sl = 0; sl < g.nslots; ++sl) {
             const bool a = (ma >> sl) & 1u, in = (mi >> sl) & 1u;
@@ -572,9 +603,8 @@ hmg_status Solver::run_bulk(int max_iter, double tol, hmg_info* info, double K[9
             if (a) {
                 eps_comp[sl] = eps32[sl];
                 if (eps32[sl] < thetaA || since_best[sl] >= stall) to_outer_a |= 1u << sl;
-            } else {
-                inner_n[sl] += blk;
-                if (eps32[sl] < eta * outer_eps[sl] || since_best[sl] >= stall) to_outer_i |= 1u << sl;
+            } else if (eps32[sl] < eta * outer_eps[sl] || since_best[sl] >= stall) {
+                to_outer_i |= 1u << sl;
             }
         }
         if (to_outer_a) HMG_TRACED(HMG_K_OTHER, 0.0, launch_widen(g, to_outer_a, s->f32buf, s->tau64, st));
@@ -582,6 +612,8 @@ hmg_status Solver::run_bulk(int max_iter, double tol, hmg_info* info, double K[9
         for (int sl = 0; sl < g.nslots; ++sl)
             if (((to_outer_a | to_outer_i) >> sl) & 1u) state[sl] = PH_OUTER;
     }
+    cudaEventDestroy(ready);
+    if (err != HMG_OK) return err;
     unsigned left = 0;
     for (int sl = 0; sl < g.nslots; ++sl)
         if (status[sl] == HMG_NOT_CONVERGED) {

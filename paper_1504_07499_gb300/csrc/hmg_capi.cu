@@ -109,6 +109,7 @@ hmg_status hmg_create(hmg_ctx** out, int device, size_t budget) {
     hmg_ctx* c = new hmg_ctx();
     c->device = device;
     cudaError_t e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->stream64, cudaStreamNonBlocking);
     if (e != cudaSuccess) {
         delete c;
         return cuda_status(e, "stream create");
@@ -132,6 +133,8 @@ hmg_status hmg_destroy(hmg_ctx* ctx) {
         cudaStreamSynchronize(ctx->stream);
         ctx->solve.free_all(ctx);
         ctx->plans.clear();
+        cudaStreamSynchronize(ctx->stream64);
+        cudaStreamDestroy(ctx->stream64);
         cudaStreamDestroy(ctx->stream);
     }
     delete ctx;
@@ -298,7 +301,8 @@ hmg_status hmg_solve_fields(hmg_ctx* ctx, const uint8_t* phase, int N, double km
     Solver sv{g, &ctx->solve, ctx->stream, ctx->tracer.on ? &ctx->tracer : nullptr};
     hmg_info local;
     memset(&local, 0, sizeof(local));
-    hmg_status rs = fp64 ? sv.run_fp64(max_iter, tol, &local, K_out) : sv.run_bulk(max_iter, tol, &local, K_out);
+    hmg_status rs = fp64 ? sv.run_fp64(max_iter, tol, &local, K_out)
+                         : sv.run_bulk(max_iter, tol, &local, K_out, ctx->stream64);
     if (rs == HMG_CUDA_ERROR) return rs;
     st = check_launch(ctx, "solve");
     if (st != HMG_OK) return st;

@@ -10,7 +10,7 @@
 namespace hmg {
 
 namespace {
-enum { PH_A = 0, PH_OUTER = 1, PH_INNER = 2, PH_DONE = 3 };
+enum { PH_A = 0, PH_OUTER = 1, PH_EQ = 2, PH_INNER = 3, PH_DONE = 4 };
 constexpr int kSideStreams = 16;
 constexpr double kEta = 1e-4;       // correction sweeps reduce the FP64 residual by this factor
 constexpr int kStall = 24;          // sweeps without a new best FP32 residual = FP32 floor
@@ -22,7 +22,8 @@ hmg_status cerr(cudaError_t e, const char* what) {
 }
 }  // namespace
 
-Engine::Engine(hmg_ctx* c, cudaStream_t s, bool graph) : ctx(c), st(s), use_graph(graph) {
+Engine::Engine(hmg_ctx* c, cudaStream_t s, cudaStream_t s64, bool graph) : ctx(c), st(s), st64(s64), use_graph(graph) {
+    cudaEventCreateWithFlags(&ready, cudaEventDisableTiming);
     for (int i = 0; i < kSideStreams; ++i) {
         cudaStream_t x;
         if (cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking) == cudaSuccess) side.push_back(x);
@@ -31,6 +32,8 @@ Engine::Engine(hmg_ctx* c, cudaStream_t s, bool graph) : ctx(c), st(s), use_grap
 
 Engine::~Engine() {
     cudaStreamSynchronize(st);
+    cudaStreamSynchronize(st64);
+    cudaEventDestroy(ready);
     for (auto& e : entries) e->st.free_all(ctx);
     if (exec) cudaGraphExecDestroy(exec);
     for (cudaStream_t x : side) cudaStreamDestroy(x);
@@ -46,7 +49,7 @@ hmg_status Engine::grow(int need) {
     int* hf = nullptr;
     double* hr = nullptr;
     if (cudaMalloc(&d, sizeof(int) * 4 * nc) != cudaSuccess || cudaMallocHost(&hf, sizeof(int) * 4 * nc) != cudaSuccess ||
-        cudaMallocHost(&hr, sizeof(double) * 16 * nc) != cudaSuccess) {
+        cudaMallocHost(&hr, sizeof(double) * 64 * nc) != cudaSuccess) {
         cudaGetLastError();
         if (d) cudaFree(d);
         if (hf) cudaFreeHost(hf);
@@ -123,68 +126,6 @@ void Engine::remove(Entry* e) {
     dirty = true;
 }
 
-// FP64 defect-correction sweeps (r = T tau64 + b - tau64) and equilibrium tests.
-hmg_status Engine::fp64_phase() {
-    std::vector<Entry*> todo;
-    for (auto& up : entries) {
-        Entry* e = up.get();
-        if (e->finished) continue;
-        unsigned mo = 0;
-        for (int sl = 0; sl < 3; ++sl)
-            if (e->sm[sl].state == PH_OUTER) mo |= 1u << sl;
-        if (!mo) continue;
-        Solver sv{e->g, &e->st, st, nullptr};
-        sv.sweep<double>(mo, e->st.tau64, e->st.spec64, Z_ITER, XI_DIFF, nullptr, e->st.f32buf, e->st.r32, 0);
-        cudaMemcpyAsync(hred + 16 * e->index, e->st.red, 3 * sizeof(double), cudaMemcpyDeviceToHost, st);
-        todo.push_back(e);
-    }
-    if (todo.empty()) return HMG_OK;
-    hmg_status s = cerr(cudaStreamSynchronize(st), "FP64 sweeps");
-    if (s != HMG_OK) return s;
-    for (Entry* e : todo) {
-        Solver sv{e->g, &e->st, st, nullptr};
-        unsigned eqm = 0, mo = 0;
-        for (int sl = 0; sl < 3; ++sl) {
-            SlotSM& m = e->sm[sl];
-            if (m.state != PH_OUTER) continue;
-            mo |= 1u << sl;
-            ++m.iters;
-            ++m.it64;
-            m.eps_comp = sv.eps_from_sum(hred[16 * e->index + sl], sl);
-            m.outer_eps = m.eps_comp;
-            if (!std::isfinite(m.eps_comp)) {
-                m.status = HMG_DIVERGED;
-                m.state = PH_DONE;
-            } else if (m.eps_comp < e->tol) {
-                eqm |= 1u << sl;
-            }
-        }
-        if (eqm) {
-            double eps[3], flux[3][3];
-            if (!sv.check_eq<double>(eqm, e->st.tau64, e->st.spec64, eps, flux)) return HMG_CUDA_ERROR;
-            for (int sl = 0; sl < 3; ++sl)
-                if ((eqm >> sl) & 1u) {
-                    e->sm[sl].eps_eq = eps[sl];
-                    memcpy(e->sm[sl].flux, flux[sl], sizeof(flux[sl]));
-                    if (eps[sl] < e->tol) {
-                        e->sm[sl].status = HMG_OK;
-                        e->sm[sl].state = PH_DONE;
-                    }
-                }
-        }
-        for (int sl = 0; sl < 3; ++sl) {
-            SlotSM& m = e->sm[sl];
-            if (((mo >> sl) & 1u) && m.state == PH_OUTER) {
-                m.state = PH_INNER;
-                m.best = INFINITY;
-                m.since_best = 0;
-                ++e->rounds;
-            }
-        }
-    }
-    return HMG_OK;
-}
-
 // The FP32 block of one entry: kResidualEvery sweeps under the per-slot flags, the last
 // one with the residual, then the residual sums of the three gradients.
 static void block_launches(const Entry* e, int* dflags, cudaStream_t s) {
@@ -244,8 +185,12 @@ hmg_status Engine::capture() {
     return HMG_OK;
 }
 
-hmg_status Engine::fp32_block() {
-    bool any = false;
+// One tick: the FP64 work of every entry (equilibrium tests, then defect-correction
+// sweeps r = T tau64 + b - tau64) on the second stream, next to the FP32 block graph on
+// the main stream; one synchronization; then every gradient moves on.
+hmg_status Engine::tick_launch_and_update() {
+    // per-slot flags of the FP32 block
+    bool any32 = false, any64 = false;
     for (auto& up : entries) {
         Entry* e = up.get();
         int* f = hflags + 4 * e->index;
@@ -253,39 +198,102 @@ hmg_status Engine::fp32_block() {
         for (int sl = 0; sl < 3; ++sl) {
             const int ph = e->finished ? PH_DONE : e->sm[sl].state;
             f[sl] = ph == PH_A ? (SF_ACTIVE | SF_ADDB) : ph == PH_INNER ? (SF_ACTIVE | SF_ADDR) : 0;
-            any = any || f[sl] != 0;
+            any32 = any32 || f[sl] != 0;
+            any64 = any64 || ph == PH_OUTER || ph == PH_EQ;
         }
     }
-    if (!any) return HMG_OK;
-    hmg_status s = cerr(cudaMemcpyAsync(dflags, hflags, sizeof(int) * 4 * entries.size(), cudaMemcpyHostToDevice, st),
-                        "flags");
-    if (s != HMG_OK) return s;
-    if (use_graph) {
-        if (dirty || !exec) {
-            s = capture();
-            if (s != HMG_OK) return s;
+    // FP64 work after the main stream's pending phase transitions
+    std::vector<unsigned> me(entries.size(), 0u), mo(entries.size(), 0u);
+    if (any64) {
+        cudaEventRecord(ready, st);
+        cudaStreamWaitEvent(st64, ready, 0);
+        for (auto& up : entries) {
+            Entry* e = up.get();
+            if (e->finished) continue;
+            for (int sl = 0; sl < 3; ++sl) {
+                if (e->sm[sl].state == PH_EQ) me[e->index] |= 1u << sl;
+                if (e->sm[sl].state == PH_OUTER) mo[e->index] |= 1u << sl;
+            }
+            if (!me[e->index] && !mo[e->index]) continue;
+            Solver sv{e->g, &e->st, st64, nullptr, e->st.partial3, e->st.partial3};
+            if (me[e->index]) sv.equilibrium<double>(me[e->index], e->st.tau64, e->st.spec64);
+            if (mo[e->index])
+                sv.sweep<double>(mo[e->index], e->st.tau64, e->st.spec64, Z_ITER, XI_DIFF, nullptr, e->st.f32buf,
+                                 e->st.r32, 48);
+            cudaMemcpyAsync(hred + 64 * e->index + 16, e->st.red + 16, 40 * sizeof(double), cudaMemcpyDeviceToHost,
+                            st64);
         }
-        s = cerr(cudaGraphLaunch(exec, st), "graph launch");
+    }
+    if (any32) {
+        hmg_status s = cerr(cudaMemcpyAsync(dflags, hflags, sizeof(int) * 4 * entries.size(), cudaMemcpyHostToDevice, st),
+                            "flags");
         if (s != HMG_OK) return s;
-        ++graph_launches;
-    } else {
-        for (auto& up : entries) block_launches(up.get(), dflags, st);
+        if (use_graph) {
+            if (dirty || !exec) {
+                s = capture();
+                if (s != HMG_OK) return s;
+            }
+            s = cerr(cudaGraphLaunch(exec, st), "graph launch");
+            if (s != HMG_OK) return s;
+            ++graph_launches;
+        } else {
+            for (auto& up : entries) block_launches(up.get(), dflags, st);
+        }
+        for (auto& up : entries)
+            cudaMemcpyAsync(hred + 64 * up->index, up->st.red, 3 * sizeof(double), cudaMemcpyDeviceToHost, st);
     }
-    for (auto& up : entries)
-        cudaMemcpyAsync(hred + 16 * up->index + 8, up->st.red, 3 * sizeof(double), cudaMemcpyDeviceToHost, st);
-    s = cerr(cudaStreamSynchronize(st), "FP32 block");
+    hmg_status s = cerr(cudaStreamSynchronize(st), "FP32 block");
+    if (s == HMG_OK) s = cerr(cudaStreamSynchronize(st64), "FP64 work");
     if (s != HMG_OK) return s;
     for (auto& up : entries) {
         Entry* e = up.get();
         if (e->finished) continue;
+        const double* h = hred + 64 * e->index;
         Solver sv{e->g, &e->st, st, nullptr};
+        for (int sl = 0; sl < 3; ++sl) {
+            SlotSM& m = e->sm[sl];
+            if ((me[e->index] >> sl) & 1u) {   // equilibrium test of the FP64 master field
+                double nrm = 0.0;
+                for (int c = 0; c < 3; ++c) {
+                    m.flux[c] = h[16 + sl * 3 + c] / (double)e->g.N3;
+                    nrm += m.flux[c] * m.flux[c];
+                }
+                m.eps_eq = std::sqrt(h[32 + sl]) / std::sqrt(nrm);
+                if (m.eps_eq < e->tol) {
+                    m.status = HMG_OK;
+                    m.state = PH_DONE;
+                } else {
+                    m.state = PH_INNER;
+                    m.best = INFINITY;
+                    m.since_best = 0;
+                    ++e->rounds;
+                }
+            }
+            if ((mo[e->index] >> sl) & 1u) {   // FP64 correction sweep
+                ++m.iters;
+                ++m.it64;
+                m.eps_comp = sv.eps_from_sum(h[48 + sl], sl);
+                m.outer_eps = m.eps_comp;
+                if (!std::isfinite(m.eps_comp)) {
+                    m.status = HMG_DIVERGED;
+                    m.state = PH_DONE;
+                } else if (m.eps_comp < e->tol) {
+                    m.state = PH_EQ;
+                } else {
+                    m.state = PH_INNER;
+                    m.best = INFINITY;
+                    m.since_best = 0;
+                    ++e->rounds;
+                }
+            }
+        }
         unsigned to_a = 0, to_i = 0;
         for (int sl = 0; sl < 3; ++sl) {
             SlotSM& m = e->sm[sl];
             const int fl = hflags[4 * e->index + sl];
             if (!fl) continue;
             m.iters += kResidualEvery;
-            m.eps32 = sv.eps_from_sum(hred[16 * e->index + 8 + sl], sl);
+            m.eps32 = sv.eps_from_sum(h[sl], sl);
             if (!std::isfinite(m.eps32)) {
                 m.status = HMG_DIVERGED;
                 m.state = PH_DONE;
@@ -297,7 +305,7 @@ hmg_status Engine::fp32_block() {
             } else {
                 m.since_best += kResidualEvery;
             }
-            if (m.state == PH_A) {
+            if (fl & SF_ADDB) {   // plain phase
                 m.eps_comp = m.eps32;
                 if (m.eps32 < std::max(e->tol, 1e-6) || m.since_best >= kStall) to_a |= 1u << sl;
             } else if (m.eps32 < kEta * m.outer_eps || m.since_best >= kStall) {
@@ -350,9 +358,7 @@ void Engine::finish_entry(Entry* e) {
 }
 
 hmg_status Engine::tick() {
-    hmg_status s = fp64_phase();
-    if (s != HMG_OK) return s;
-    s = fp32_block();
+    hmg_status s = tick_launch_and_update();
     if (s != HMG_OK) return s;
     for (auto& up : entries) {
         Entry* e = up.get();

@@ -3,7 +3,7 @@
 //
 // Each engine tick runs, for every entry:
 //   * FP64 defect-correction sweeps and equilibrium tests of the gradients that need
-//     them (direct launches, rare);
+//     them (direct launches on a second stream, overlapping the FP32 block);
 //   * one block of kResidualEvery FP32 sweeps for every gradient in the plain or the
 //     correction phase.  Which gradients are active and which sweep form they use are
 //     per-slot flags in device memory, so the block for all entries is one CUDA graph,
@@ -53,7 +53,7 @@ struct Entry {
 
 class Engine {
    public:
-    Engine(hmg_ctx* ctx, cudaStream_t stream, bool use_graph);
+    Engine(hmg_ctx* ctx, cudaStream_t stream, cudaStream_t stream64, bool use_graph);
     ~Engine();
     // Allocate device state for one RVE and copy its phase grid (host or device).
     hmg_status add(long long id, const uint8_t* phase, int N, const double k[3], double tol, int max_iter,
@@ -69,18 +69,19 @@ class Engine {
     long long graph_launches = 0;
 
    private:
-    hmg_status fp64_phase();
-    hmg_status fp32_block();
+    hmg_status tick_launch_and_update();
     hmg_status capture();
     void finish_entry(Entry* e);
     hmg_ctx* ctx;
     cudaStream_t st;
+    cudaStream_t st64;     // FP64 work, overlapped with the FP32 block
+    cudaEvent_t ready;
     bool use_graph;
     std::vector<std::unique_ptr<Entry>> entries;
     std::vector<cudaStream_t> side;
     int* dflags = nullptr;      // 4 ints per entry
     int* hflags = nullptr;      // pinned
-    double* hred = nullptr;     // pinned, 16 doubles per entry
+    double* hred = nullptr;     // pinned, 64 doubles per entry (the entry's residual sums)
     int cap = 0;
     cudaGraphExec_t exec = nullptr;
     bool dirty = true;

@@ -44,9 +44,11 @@ struct SolveState {
     float* f32buf = nullptr;
     float* r32 = nullptr;
     void* spec32 = nullptr;
-    double* partial = nullptr;
-    double* partial2 = nullptr;
-    double* red = nullptr;   // [0,16): sweep sums, [16,32): flux sums, [32,48): eq sums
+    double* partial = nullptr;    // FP32 sweeps (x inverse residual)
+    double* partial2 = nullptr;   // equilibrium norm (z pass)
+    double* partial3 = nullptr;   // FP64 work: correction sweep residual and flux average
+    double* red = nullptr;   // [0,16): FP32 sweep sums, [16,32): flux sums, [32,48): eq sums,
+                             // [48,56): FP64 sweep sums
     bool ensure(::hmg_ctx* c, int N, bool fp64, int nslots);
     void free_all(::hmg_ctx* c);
 };
@@ -88,6 +90,8 @@ struct Solver {
     SolveState* s;
     cudaStream_t st;
     Tracer* tr = nullptr;
+    double* psweep = nullptr;   // partial sums of sweeps (nullptr: s->partial)
+    double* pflux = nullptr;    // partial sums of the flux average (nullptr: s->partial)
     // one sweep of steps 2-7; residual modes leave the per-slot sums at red[red_off + slot]
     template <typename R>
     void sweep(unsigned mask, R* field, void* spec, int zmode, int ximode, const float* r32in, float* d32,
@@ -99,7 +103,7 @@ struct Solver {
     bool fetch(double* h, int off, int count);
     double eps_from_sum(double sum, int slot) const;
     hmg_status run_fp64(int max_iter, double tol, hmg_info* info, double K[9]);
-    hmg_status run_bulk(int max_iter, double tol, hmg_info* info, double K[9]);
+    hmg_status run_bulk(int max_iter, double tol, hmg_info* info, double K[9], cudaStream_t st64);
     hmg_status finish(const int status[3], const int iters[3], const int it64[3], const double eps_comp[3],
                       const double eps_eq[3], const double flux[3][3], int rounds, hmg_info* info, double K[9]);
 };
@@ -112,6 +116,7 @@ struct Server;
 struct hmg_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
+    cudaStream_t stream64 = nullptr;   // FP64 work overlapped with the FP32 sweeps
     size_t budget = 0;
     size_t used = 0;
     std::map<void*, size_t> sizes;

@@ -96,7 +96,7 @@ void Server::loop() {
     std::unique_ptr<Engine> eng;
     if (cs == HMG_OK) {
         cudaSetDevice(device);
-        eng = std::make_unique<Engine>(ctx, ctx->stream, true);
+        eng = std::make_unique<Engine>(ctx, ctx->stream, ctx->stream64, true);
     }
     std::map<Entry*, uint64_t> running;
     for (;;) {
@@ -272,7 +272,7 @@ hmg_status hmg_solve_batch(hmg_ctx* ctx, int count, const uint8_t* const* phases
     cudaSetDevice(ctx->device);
     auto t0 = now_s();
     ctx->solve.free_all(ctx);   // the engine holds its own per-RVE state
-    Engine eng(ctx, ctx->stream, true);
+    Engine eng(ctx, ctx->stream, ctx->stream64, true);
     int next = 0;
     std::map<Entry*, int> live;
     while (next < count || !live.empty()) {
