@@ -220,12 +220,14 @@ hmg_status hmg_poll(hmg_ctx* ctx, uint64_t ticket, double K_out[9], hmg_info* in
 
 /* ---- kernel variants (autotuning) --------------------------------------------- */
 
-/* The FP32 path has two z-pass kernels for grid sizes 64, 96, 128, 192 and 256
- * (variant 0: one thread holds the three components of its modes; variant 1: one
- * thread group per component, projections summed through shared memory).  The first
- * FP32 solve at a size times both on the device and keeps the faster.
- * hmg_set_variant pins `variant` (0 or 1) for size N, or clears the choice (-1) so
- * that the next solve times them again.  Both give the same results to rounding. */
+/* The FP32 path has kernel variants for grid sizes 64, 96, 128, 192 and 256, chosen by
+ * timing on the device at the first FP32 solve of a size and kept per context:
+ *   bit 0: z pass -- 0: one thread holds the three components of its modes; 1: one
+ *          thread group per component, projections summed through shared memory;
+ *   bit 1: x and y passes (sizes 128, 192, 256) -- 0: separate passes; 1: one
+ *          thread-block-cluster kernel per direction (distributed shared memory).
+ * hmg_set_variant pins `variant` (0 .. 3) for size N, or clears the choice (-1) so
+ * that the next solve times them again.  All give the same results to rounding. */
 hmg_status hmg_set_variant(hmg_ctx* ctx, int N, int variant);
 
 /* The variant chosen for size N (-1 if none yet). */

@@ -8,10 +8,12 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <functional>
 #include <map>
 #include <memory>
 #include <mutex>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/hmg.h"
@@ -153,36 +155,59 @@ GridDesc make_desc(const GridPlan& gp, bool fp64, const double k[3], const uint8
     return g;
 }
 
+static float time_launches(cudaStream_t st, const std::function<void()>& f, int reps) {
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    f();   // warm-up
+    cudaEventRecord(a, st);
+    for (int r = 0; r < reps; ++r) f();
+    cudaEventRecord(b, st);
+    cudaEventSynchronize(b);
+    float ms = 1e30f;
+    if (cudaEventElapsedTime(&ms, a, b) != cudaSuccess) ms = 1e30f;
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    return ms;
+}
+
 int autotune_z(::hmg_ctx* c, GridDesc g, SolveState* s, cudaStream_t st) {
     auto it = c->ztune.find(g.N);
     if (it != c->ztune.end()) return it->second;
     int best = 0;
-    if (!s->spec32 || !fast_z_ctas(g)) {
+    if (!s->spec32 || !s->f32buf) {
         c->ztune[g.N] = best;
         return best;
     }
     const unsigned all = (1u << g.nslots) - 1u;
-    cudaMemsetAsync(s->spec32, 0, (size_t)g.nslots * 3 * g.N3 * sizeof(float), st);
-    cudaEvent_t a, b;
-    cudaEventCreate(&a);
-    cudaEventCreate(&b);
-    float best_ms = 1e30f;
-    for (int v = 0; v < 2; ++v) {
-        g.zvar = v;
-        launch_z_pass<float>(g, Z_ITER, all, s->spec32, nullptr, st);   // warm-up
-        cudaEventRecord(a, st);
-        for (int r = 0; r < 4; ++r) launch_z_pass<float>(g, Z_ITER, all, s->spec32, nullptr, st);
-        cudaEventRecord(b, st);
-        cudaEventSynchronize(b);
-        float ms = 0.f;
-        if (cudaEventElapsedTime(&ms, a, b) == cudaSuccess && ms < best_ms) {
-            best_ms = ms;
-            best = v;
+    const size_t bytes = (size_t)g.nslots * 3 * g.N3 * sizeof(float);
+    cudaMemsetAsync(s->spec32, 0, bytes, st);
+    cudaMemsetAsync(s->f32buf, 0, bytes, st);
+    // z pass: two kernels
+    int zbest = 0;
+    if (fast_z_ctas(g)) {
+        float zms[2];
+        for (int v = 0; v < 2; ++v) {
+            g.zvar = v;
+            zms[v] = time_launches(st, [&] { launch_z_pass<float>(g, Z_ITER, all, s->spec32, nullptr, st); }, 4);
         }
+        zbest = zms[1] < zms[0] ? 1 : 0;
     }
-    cudaEventDestroy(a);
-    cudaEventDestroy(b);
+    // x and y passes: fused cluster kernels or separate passes
+    int xybest = 0;
+    if (fused_cluster(g.N)) {
+        float xyms[2];
+        for (int v = 0; v < 2; ++v) {
+            g.xyvar = v;
+            xyms[v] = time_launches(st, [&] {
+                launch_xy_forward<float>(g, XF_POLARIZE, all, s->f32buf, s->spec32, nullptr, st);
+                launch_yx_inverse<float>(g, XI_INPLACE, all, s->spec32, s->f32buf, nullptr, nullptr, nullptr, nullptr, st);
+            }, 3);
+        }
+        xybest = xyms[1] < xyms[0] ? 1 : 0;
+    }
     cudaGetLastError();
+    best = zbest | (xybest << 1);
     c->ztune[g.N] = best;
     return best;
 }
@@ -362,18 +387,29 @@ void Solver::sweep(unsigned mask, R* field, void* spec, int zmode, int ximode, c
                    float* d32, float* r32out, int red_off) {
     const double f = (double)popc(mask) * 3.0 * (double)g.N3;   // field elements moved per array
     const double F = sizeof(R);
-    HMG_TRACED(HMG_K_X_FORWARD, f * 2 * F + (double)g.N3,
-               launch_x_forward<R>(g, XF_POLARIZE, mask, field, spec, nullptr, st));
-    HMG_TRACED(HMG_K_Y_FORWARD, f * 2 * F, launch_y_pass<R>(g, true, mask, spec, st));
-    HMG_TRACED(HMG_K_Z_GREEN, f * 2 * F, launch_z_pass<R>(g, zmode, mask, spec, nullptr, st));
-    HMG_TRACED(HMG_K_Y_INVERSE, f * 2 * F, launch_y_pass<R>(g, false, mask, spec, st));
+    const bool fused = std::is_same<R, float>::value && g.xyvar == 1 && fused_cluster(g.N) != 0;
+    double* pb = psweep ? psweep : s->partial;
     double xb = f * 2 * F;                                       // spectrum in, field out
     if (ximode == XI_INPLACE_RES) xb += f * F;                  // old field for the residual
     if (ximode == XI_ADD_R_RES) xb += f * F + f * 4;            // old field and r
     if (ximode == XI_ADD_R) xb += f * 4;                         // r
     if (ximode == XI_DIFF) xb = f * F + f * F + 2 * f * 4;      // spectrum, old field, d and r out
-    double* pb = psweep ? psweep : s->partial;
-    HMG_TRACED(HMG_K_X_INVERSE, xb, launch_x_inverse<R>(g, ximode, mask, spec, field, r32in, d32, r32out, pb, st));
+    if (fused) {
+        // x+y forward and y+x inverse: one cluster kernel each
+        HMG_TRACED(HMG_K_X_FORWARD, f * 2 * F + (double)g.N3,
+                   launch_xy_forward<R>(g, XF_POLARIZE, mask, field, spec, nullptr, st));
+        HMG_TRACED(HMG_K_Z_GREEN, f * 2 * F, launch_z_pass<R>(g, zmode, mask, spec, nullptr, st));
+        HMG_TRACED(HMG_K_X_INVERSE, xb,
+                   launch_yx_inverse<R>(g, ximode, mask, spec, field, r32in, d32, r32out, pb, st));
+    } else {
+        HMG_TRACED(HMG_K_X_FORWARD, f * 2 * F + (double)g.N3,
+                   launch_x_forward<R>(g, XF_POLARIZE, mask, field, spec, nullptr, st));
+        HMG_TRACED(HMG_K_Y_FORWARD, f * 2 * F, launch_y_pass<R>(g, true, mask, spec, st));
+        HMG_TRACED(HMG_K_Z_GREEN, f * 2 * F, launch_z_pass<R>(g, zmode, mask, spec, nullptr, st));
+        HMG_TRACED(HMG_K_Y_INVERSE, f * 2 * F, launch_y_pass<R>(g, false, mask, spec, st));
+        HMG_TRACED(HMG_K_X_INVERSE, xb,
+                   launch_x_inverse<R>(g, ximode, mask, spec, field, r32in, d32, r32out, pb, st));
+    }
     if (ximode == XI_INPLACE_RES || ximode == XI_ADD_R_RES || ximode == XI_DIFF)
         HMG_TRACED(HMG_K_OTHER, 0.0, launch_reduce(pb, g.nslots, x_ctas_for<R>(g), 1, s->red + red_off, st));
 }
@@ -382,10 +418,15 @@ template <typename R>
 void Solver::equilibrium(unsigned mask, const R* field, void* spec) {
     const double f = (double)popc(mask) * 3.0 * (double)g.N3;
     const double F = sizeof(R);
+    const bool fused = std::is_same<R, float>::value && g.xyvar == 1 && fused_cluster(g.N) != 0;
     double* pb = pflux ? pflux : s->partial;
-    HMG_TRACED(HMG_K_EQ_X, f * 2 * F + (double)g.N3, launch_x_forward<R>(g, XF_FLUX, mask, field, spec, pb, st));
+    if (fused) {
+        HMG_TRACED(HMG_K_EQ_X, f * 2 * F + (double)g.N3, launch_xy_forward<R>(g, XF_FLUX, mask, field, spec, pb, st));
+    } else {
+        HMG_TRACED(HMG_K_EQ_X, f * 2 * F + (double)g.N3, launch_x_forward<R>(g, XF_FLUX, mask, field, spec, pb, st));
+    }
     HMG_TRACED(HMG_K_OTHER, 0.0, launch_reduce(pb, g.nslots, x_ctas_for<R>(g), 3, s->red + 16, st));
-    HMG_TRACED(HMG_K_Y_FORWARD, f * 2 * F, launch_y_pass<R>(g, true, mask, spec, st));
+    if (!fused) HMG_TRACED(HMG_K_Y_FORWARD, f * 2 * F, launch_y_pass<R>(g, true, mask, spec, st));
     HMG_TRACED(HMG_K_EQ_Z, f * F, launch_z_pass<R>(g, Z_EQ, mask, spec, s->partial2, st));
     HMG_TRACED(HMG_K_OTHER, 0.0, launch_reduce(s->partial2, g.nslots, z_ctas_for<R>(g), 1, s->red + 32, st));
 }

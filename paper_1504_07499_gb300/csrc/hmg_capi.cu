@@ -80,7 +80,11 @@ hmg_status prepare(hmg_ctx* ctx, const uint8_t* phase, int N, const double k[3],
     hmg_status st = cuda_status(copy_in(ctx->solve.phase, phase, N3, ctx->stream), "phase copy");
     if (st != HMG_OK) return st;
     *g = make_desc(*gp, fp64, k, ctx->solve.phase, nslots);
-    if (!fp64) g->zvar = autotune_z(ctx, *g, &ctx->solve, ctx->stream);
+    if (!fp64) {
+        const int v = autotune_z(ctx, *g, &ctx->solve, ctx->stream);
+        g->zvar = v & 1;
+        g->xyvar = (v >> 1) & 1;
+    }
     return HMG_OK;
 }
 
@@ -145,8 +149,8 @@ size_t hmg_footprint(int N, hmg_precision p) { return state_bytes(N, p == HMG_FP
 
 hmg_status hmg_set_variant(hmg_ctx* ctx, int N, int variant) {
     g_last_error.clear();
-    if (!ctx || !valid_N(N) || variant < -1 || variant > 1) {
-        set_error("bad context, N or variant (-1, 0 or 1)");
+    if (!ctx || !valid_N(N) || variant < -1 || variant > 3) {
+        set_error("bad context, N or variant (-1 .. 3)");
         return HMG_INVALID_ARG;
     }
     if (variant < 0) ctx->ztune.erase(N);
@@ -424,7 +428,11 @@ static hmg_status fft_common(hmg_ctx* ctx, int N, int count, hmg_precision preci
     }
     const double k[3] = {1.0, 1.0, 1.0};
     GridDesc g = make_desc(*gp, fp64, k, ctx->solve.phase, 1);
-    if (!fp64) g.zvar = autotune_z(ctx, g, &ctx->solve, ctx->stream);
+    if (!fp64) {
+        const int v = autotune_z(ctx, g, &ctx->solve, ctx->stream);
+        g.zvar = v & 1;
+        g.xyvar = (v >> 1) & 1;
+    }
     SolveState& s = ctx->solve;
     const long long N3 = g.N3;
     double* d64 = s.tau64;          // 3 N^3 doubles: staging of one group of three grids
@@ -444,8 +452,7 @@ static hmg_status fft_common(hmg_ctx* ctx, int N, int count, hmg_precision preci
                 float* f = s.f32buf;
                 float* sp = reinterpret_cast<float*>(s.spec32);
                 launch_convert<float>(d64, f, 3 * N3, ctx->stream);
-                launch_x_forward<float>(g, XF_PLAIN, 1u, f, sp, nullptr, ctx->stream);
-                launch_y_pass<float>(g, true, 1u, sp, ctx->stream);
+                launch_xy_forward<float>(g, XF_PLAIN, 1u, f, sp, nullptr, ctx->stream);
                 launch_z_pass<float>(g, Z_FWD, 1u, sp, nullptr, ctx->stream);
                 launch_convert_back<float>(sp, dsp, 3 * N3, ctx->stream);
                 st = cuda_status(copy_out(out + (size_t)base * N3, dsp, cnt * N3 * sizeof(double), ctx->stream), "copy out");
@@ -462,8 +469,7 @@ static hmg_status fft_common(hmg_ctx* ctx, int N, int count, hmg_precision preci
                 float* sp = reinterpret_cast<float*>(s.spec32);
                 launch_convert<float>(d64, sp, 3 * N3, ctx->stream);
                 launch_z_pass<float>(g, Z_INV, 1u, sp, nullptr, ctx->stream);
-                launch_y_pass<float>(g, false, 1u, sp, ctx->stream);
-                launch_x_inverse<float>(g, XI_PLAIN, 1u, sp, f, nullptr, nullptr, nullptr, nullptr, ctx->stream);
+                launch_yx_inverse<float>(g, XI_PLAIN, 1u, sp, f, nullptr, nullptr, nullptr, nullptr, ctx->stream);
                 launch_convert_back<float>(f, d64, 3 * N3, ctx->stream);
                 st = cuda_status(copy_out(out + (size_t)base * N3, d64, cnt * N3 * sizeof(double), ctx->stream), "copy out");
             }

@@ -105,7 +105,11 @@ hmg_status Engine::add(long long id, const uint8_t* phase, int N, const double k
         return s;
     }
     e->g = make_desc(*e->plan, false, k, e->st.phase, 3);
-    e->g.zvar = autotune_z(ctx, e->g, &e->st, st);
+    {
+        const int v = autotune_z(ctx, e->g, &e->st, st);
+        e->g.zvar = v & 1;
+        e->g.xyvar = (v >> 1) & 1;
+    }
     launch_init_tau<float>(e->g, 7u, e->st.f32buf, st);
     e->index = (int)entries.size();
     if (out) *out = e.get();
@@ -134,11 +138,9 @@ static void block_launches(const Entry* e, int* dflags, cudaStream_t s) {
     SolveState st = e->st;
     for (int b = 0; b < kResidualEvery; ++b) {
         gf.resid = b == kResidualEvery - 1;
-        launch_x_forward<float>(gf, XF_POLARIZE, 7u, st.f32buf, st.spec32, nullptr, s);
-        launch_y_pass<float>(gf, true, 7u, st.spec32, s);
+        launch_xy_forward<float>(gf, XF_POLARIZE, 7u, st.f32buf, st.spec32, nullptr, s);
         launch_z_pass<float>(gf, Z_ITER, 7u, st.spec32, nullptr, s);
-        launch_y_pass<float>(gf, false, 7u, st.spec32, s);
-        launch_x_inverse<float>(gf, XI_ADD_R_RES, 7u, st.spec32, st.f32buf, st.r32, nullptr, nullptr, st.partial, s);
+        launch_yx_inverse<float>(gf, XI_ADD_R_RES, 7u, st.spec32, st.f32buf, st.r32, nullptr, nullptr, st.partial, s);
     }
     launch_reduce(st.partial, 3, x_ctas_for<float>(gf), 1, st.red, s);
 }

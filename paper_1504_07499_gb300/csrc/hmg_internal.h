@@ -38,6 +38,7 @@ struct GridDesc {
     int rows;              // x-pass rows per CTA
     int Py, Pz;            // columns per CTA in the y and z passes
     int zvar;              // z-pass kernel variant of the register-resident path (autotuned)
+    int xyvar;             // 1: fused x + y cluster kernels, 0: separate x and y passes (autotuned)
     // Per-slot flags in device memory (engine launches; nullptr = use the launch's
     // mask and template modes): SF_ACTIVE, SF_ADDB (add 2 k0 E at DC, plain sweep),
     // SF_ADDR (add the defect r, correction sweep).  `resid`: this launch of the x
@@ -94,6 +95,24 @@ bool fast_x_inverse(const GridDesc& g, int mode, unsigned mask, const void* spec
                     double* partial, cudaStream_t st);
 int fast_x_ctas(const GridDesc& g);
 int fast_z_ctas(const GridDesc& g);
+
+// Fused x + y passes on thread-block clusters (hmg_fused.cu, FP32); false / 0 when the
+// grid size has no fused kernels.
+int fused_cluster(int N);
+int fused_xy_ctas(const GridDesc& g);
+bool fused_xy_forward(const GridDesc& g, int mode, unsigned mask, const float* tau, void* spec, double* partial,
+                      cudaStream_t st);
+bool fused_yx_inverse(const GridDesc& g, int mode, unsigned mask, const void* spec, float* tau, const float* r32,
+                      double* partial, cudaStream_t st);
+
+// x then y forward (one fused launch where available), and y then x inverse.
+// Return true when the fused kernels ran.
+template <typename R>
+bool launch_xy_forward(const GridDesc& g, int mode, unsigned mask, const R* tau, void* spec, double* partial,
+                       cudaStream_t st);
+template <typename R>
+bool launch_yx_inverse(const GridDesc& g, int mode, unsigned mask, const void* spec, R* tau, const float* r32,
+                       float* d32, float* r32_out, double* partial, cudaStream_t st);
 
 // Sum `count` partials of each of `nslots` rows in a fixed order: out[s] = sum_i p[s*count+i].
 // `groups` > 1 splits each row into that many equal consecutive groups (out[s*groups+g]).

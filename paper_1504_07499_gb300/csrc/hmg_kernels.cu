@@ -383,6 +383,7 @@ int x_ctas(const GridDesc& g) { return (int)(3 * g.NN / g.rows); }
 int z_ctas(const GridDesc& g) { return g.N * (g.M / g.Pz); }
 
 template <> int x_ctas_for<float>(const GridDesc& g) {
+    if (g.xyvar == 1 && fused_cluster(g.N)) return fused_xy_ctas(g);
     const int f = fast_x_ctas(g);
     return f ? f : x_ctas(g);
 }
@@ -496,6 +497,28 @@ void launch_x_inverse(const GridDesc& g, int mode, unsigned mask, const void* sp
 #undef HMG_XI
 }
 
+template <typename R>
+bool launch_xy_forward(const GridDesc& g, int mode, unsigned mask, const R* tau, void* spec, double* partial,
+                       cudaStream_t st) {
+    if constexpr (std::is_same<R, float>::value) {
+        if (g.xyvar == 1 && fused_xy_forward(g, mode, mask, tau, spec, partial, st)) return true;
+    }
+    launch_x_forward<R>(g, mode, mask, tau, spec, partial, st);
+    launch_y_pass<R>(g, true, mask, spec, st);
+    return false;
+}
+
+template <typename R>
+bool launch_yx_inverse(const GridDesc& g, int mode, unsigned mask, const void* spec, R* tau, const float* r32,
+                       float* d32, float* r32_out, double* partial, cudaStream_t st) {
+    if constexpr (std::is_same<R, float>::value) {
+        if (g.xyvar == 1 && fused_yx_inverse(g, mode, mask, spec, tau, r32, partial, st)) return true;
+    }
+    launch_y_pass<R>(g, false, mask, const_cast<void*>(spec), st);
+    launch_x_inverse<R>(g, mode, mask, spec, tau, r32, d32, r32_out, partial, st);
+    return false;
+}
+
 void launch_reduce(const double* partial, int nslots, int count, int groups, double* out, cudaStream_t st) {
     k_reduce<<<nslots * groups, kThreads, 0, st>>>(partial, count, groups, out);
 }
@@ -534,6 +557,9 @@ void launch_convert_back(const R* src, double* dst, long long n, cudaStream_t st
     template void launch_x_inverse<R>(const GridDesc&, int, unsigned, const void*, R*, const float*, float*, \
                                       float*, double*, cudaStream_t);                                       \
     template void launch_init_tau<R>(const GridDesc&, unsigned, R*, cudaStream_t);                          \
+    template bool launch_xy_forward<R>(const GridDesc&, int, unsigned, const R*, void*, double*, cudaStream_t); \
+    template bool launch_yx_inverse<R>(const GridDesc&, int, unsigned, const void*, R*, const float*, float*,   \
+                                       float*, double*, cudaStream_t);                                        \
     template void launch_e_to_tau<R>(const GridDesc&, int, const double*, R*, cudaStream_t);                \
     template void launch_tau_to_e<R>(const GridDesc&, int, const R*, double*, cudaStream_t);                \
     template void launch_convert<R>(const double*, R*, long long, cudaStream_t);                            \

@@ -29,11 +29,12 @@ def ctx():
 
 
 def _rves():
-    """Mixed sizes: a generic-kernel size (32) and register-path sizes (64, 96)."""
+    """Mixed sizes: a generic-kernel size (32), register-path sizes (64, 96) and a size
+    with the fused cluster kernels (128)."""
     out = []
     for i, (N, n, f, layer, kc) in enumerate([(32, 8, 0.25, 0.3, 400.0), (64, 20, 0.3, 0.2, 40.0),
                                               (32, 5, 0.2, 0.5, 4000.0), (96, 30, 0.25, 0.3, 400.0),
-                                              (64, 12, 0.35, 0.4, 400.0)]):
+                                              (64, 12, 0.35, 0.4, 400.0), (128, 30, 0.2, 0.3, 400.0)]):
         sl = I.generate_spheres(100 + i, n, f)
         out.append((om.voxelize(sl.spheres, layer, N), N, (0.20, 0.25, kc)))
     return out

@@ -27,9 +27,9 @@ def ctx():
     c.close()
 
 
-@pytest.fixture(params=[0, 1], ids=["zvar0", "zvar1"])
+@pytest.fixture(params=[0, 1, 2, 3], ids=["z0", "z1", "z0-fusedxy", "z1-fusedxy"])
 def zvar(request, ctx):
-    """Runs a test once per z-pass kernel variant, pinned for every fast size."""
+    """Runs a test once per kernel variant (z pass, fused x + y), pinned for every fast size."""
     for n in (64, 96, 128, 192, 256):
         hmg.hmg_set_variant(ctx.handle, n, request.param)
     yield request.param
@@ -77,8 +77,8 @@ def test_fast_equilibrium_fp32(ctx, zvar):
     assert np.abs(flux + ref_mean).max() < 1e-5 * np.abs(ref_mean).max()
 
 
-def test_fast_bulk_solve_64_matches_oracle(ctx, zvar):
-    N = 64
+@pytest.mark.parametrize("N", [64, 128])
+def test_fast_bulk_solve_matches_oracle(ctx, zvar, N):
     sl = I.generate_spheres(1000, 30, 0.2)
     ph = om.voxelize(sl.spheres, 0.3, N)
     k = (0.20, 0.25, 40.0)          # contrast 200 keeps the oracle solve short
@@ -118,4 +118,4 @@ def test_autotuner_records_a_variant(ctx):
     e = np.zeros((3, N, N, N))
     e[0] = 1.0
     hmg.hmg_em_iterate(ctx.handle, ph, N, K3, (1.0, 0.0, 0.0), hmg.HMG_FP32_BULK, 1, e)
-    assert hmg.hmg_get_variant(ctx.handle, N) in (0, 1)
+    assert hmg.hmg_get_variant(ctx.handle, N) in (0, 1, 2, 3)
