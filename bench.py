@@ -170,6 +170,9 @@ def main() -> None:
                     help="single: the 256^3 RVE (default); batch: 64 mixed-size RVEs in one engine; "
                          "serve: Poisson request stream through hmg_submit/hmg_poll")
     ap.add_argument("--requests", type=int, default=48, help="serve mode: requests per arrival rate")
+    ap.add_argument("--variant", type=int, default=-1,
+                    help="pin the FP32 kernel variant of the 256^3 grid (0..3, see hmg_set_variant); "
+                         "default: autotuned on the device")
     ap.add_argument("--sweeps-only", type=int, default=0,
                     help="profiling case: voxelize, run this many sweeps of one gradient, exit")
     args = ap.parse_args()
@@ -216,6 +219,8 @@ def main() -> None:
         _, info, _ = hmg.hmg_solve(ctx.handle, phase_d, N_GRID, K_PHASES, TOL, prec)
         return info
 
+    if args.variant >= 0:
+        hmg.hmg_set_variant(ctx.handle, N_GRID, args.variant)
     if args.sweeps_only:
         hmg.hmg_voxelize(ctx.handle, sph_d, LAYER, N_GRID, phase_d)
         e = torch.zeros((3, N3), dtype=torch.float64, device="cuda")

@@ -644,7 +644,7 @@ hmg_status Solver::run_bulk(int max_iter, double tol, hmg_info* info, double K[9
             if (a) {
                 eps_comp[sl] = eps32[sl];
                 if (eps32[sl] < thetaA || since_best[sl] >= stall) to_outer_a |= 1u << sl;
-            } else if (eps32[sl] < eta * outer_eps[sl] || since_best[sl] >= stall) {
+            } else if (eps32[sl] < std::max(eta * outer_eps[sl], kInnerFloor * tol) || since_best[sl] >= stall) {
                 to_outer_i |= 1u << sl;
             }
         }

@@ -310,7 +310,7 @@ hmg_status Engine::tick_launch_and_update() {
             if (fl & SF_ADDB) {   // plain phase
                 m.eps_comp = m.eps32;
                 if (m.eps32 < std::max(e->tol, 1e-6) || m.since_best >= kStall) to_a |= 1u << sl;
-            } else if (m.eps32 < kEta * m.outer_eps || m.since_best >= kStall) {
+            } else if (m.eps32 < std::max(kEta * m.outer_eps, kInnerFloor * e->tol) || m.since_best >= kStall) {
                 to_i |= 1u << sl;
             }
         }

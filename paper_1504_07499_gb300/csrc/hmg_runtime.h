@@ -84,6 +84,11 @@ struct Tracer {
 // block computes the residual and the host reads it once per block.
 constexpr int kResidualEvery = 4;
 
+// A correction solve stops once its residual is below this fraction of the tolerance:
+// the FP64 residual that follows is then below tol, and reducing it further only costs
+// sweeps (the tolerance itself is checked in FP64).
+constexpr double kInnerFloor = 0.1;
+
 // Driver of one solve on one SolveState.
 struct Solver {
     GridDesc g;
