@@ -171,7 +171,7 @@ def main() -> None:
                          "serve: Poisson request stream through hmg_submit/hmg_poll")
     ap.add_argument("--requests", type=int, default=48, help="serve mode: requests per arrival rate")
     ap.add_argument("--variant", type=int, default=-1,
-                    help="pin the FP32 kernel variant of the 256^3 grid (0..3, see hmg_set_variant); "
+                    help="pin the FP32 kernel variant of the 256^3 grid (0..7, see hmg_set_variant); "
                          "default: autotuned on the device")
     ap.add_argument("--sweeps-only", type=int, default=0,
                     help="profiling case: voxelize, run this many sweeps of one gradient, exit")

@@ -225,9 +225,14 @@ hmg_status hmg_poll(hmg_ctx* ctx, uint64_t ticket, double K_out[9], hmg_info* in
  *   bit 0: z pass -- 0: one thread holds the three components of its modes; 1: one
  *          thread group per component, projections summed through shared memory;
  *   bit 1: x and y passes (sizes 128, 192, 256) -- 0: separate passes; 1: one
- *          thread-block-cluster kernel per direction (distributed shared memory).
- * hmg_set_variant pins `variant` (0 .. 3) for size N, or clears the choice (-1) so
- * that the next solve times them again.  All give the same results to rounding. */
+ *          thread-block-cluster kernel per direction (distributed shared memory);
+ *   bit 2: with separate passes, the sweeps of a block of FP32 sweeps are chained
+ *          (0, the default: the x inverse of one sweep and the x forward of the next
+ *          are one kernel and the field is stored only before the residual sweep) or
+ *          not (1).  Chained and unchained sweeps give bit-identical results.
+ * The autotuner chooses bits 0 and 1 and leaves bit 2 clear.  hmg_set_variant pins
+ * `variant` (0 .. 7) for size N, or clears the choice (-1) so that the next solve
+ * times them again.  All give the same results to rounding. */
 hmg_status hmg_set_variant(hmg_ctx* ctx, int N, int variant);
 
 /* The variant chosen for size N (-1 if none yet). */
@@ -245,7 +250,9 @@ typedef enum {
     HMG_K_EQ_X = 5,        /* equilibrium check: x pass with the flux average (step 1) */
     HMG_K_EQ_Z = 6,        /* equilibrium check: z pass with the divergence norm (step 1) */
     HMG_K_OTHER = 7,       /* reductions, conversions, voxelization */
-    HMG_K_COUNT = 8
+    HMG_K_X_ROUND = 8,     /* x pass inverse + update of one sweep fused with the
+                              polarization + x pass forward of the next (steps 5-7, 2-3) */
+    HMG_K_COUNT = 9
 } hmg_kernel_kind;
 
 /* Start (enable = 1, counters reset) or stop (0) timing every kernel the solver

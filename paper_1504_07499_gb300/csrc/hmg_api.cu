@@ -200,6 +200,12 @@ int autotune_z(::hmg_ctx* c, GridDesc g, SolveState* s, cudaStream_t st) {
         for (int v = 0; v < 2; ++v) {
             g.xyvar = v;
             xyms[v] = time_launches(st, [&] {
+                if (v == 0 && fast_x_ctas(g)) {   // separate passes: a chained sweep's x and y work
+                    launch_y_pass<float>(g, true, all, s->spec32, st);
+                    launch_y_pass<float>(g, false, all, s->spec32, st);
+                    fast_x_round(g, false, false, all, s->spec32, s->f32buf, nullptr, st);
+                    return;
+                }
                 launch_xy_forward<float>(g, XF_POLARIZE, all, s->f32buf, s->spec32, nullptr, st);
                 launch_yx_inverse<float>(g, XI_INPLACE, all, s->spec32, s->f32buf, nullptr, nullptr, nullptr, nullptr, st);
             }, 3);
@@ -414,6 +420,36 @@ void Solver::sweep(unsigned mask, R* field, void* spec, int zmode, int ximode, c
         HMG_TRACED(HMG_K_OTHER, 0.0, launch_reduce(pb, g.nslots, x_ctas_for<R>(g), 1, s->red + red_off, st));
 }
 
+bool Solver::chained() const { return chain_sweeps(g); }
+
+void Solver::block_sweep(unsigned mask, int b, int blk, int zmode, bool addr, const float* r32in, int red_off) {
+    const bool last = b == blk - 1;
+    const int ximode = addr ? (last ? XI_ADD_R_RES : XI_ADD_R) : (last ? XI_INPLACE_RES : XI_INPLACE);
+    if (!chained()) {
+        sweep<float>(mask, s->f32buf, s->spec32, zmode, ximode, r32in, nullptr, nullptr, red_off);
+        return;
+    }
+    const double f = (double)popc(mask) * 3.0 * (double)g.N3;   // field elements moved per array
+    const double F = sizeof(float);
+    double* pb = psweep ? psweep : s->partial;
+    if (b == 0)
+        HMG_TRACED(HMG_K_X_FORWARD, f * 2 * F + (double)g.N3,
+                   launch_x_forward<float>(g, XF_POLARIZE, mask, s->f32buf, s->spec32, nullptr, st));
+    HMG_TRACED(HMG_K_Y_FORWARD, f * 2 * F, launch_y_pass<float>(g, true, mask, s->spec32, st));
+    HMG_TRACED(HMG_K_Z_GREEN, f * 2 * F, launch_z_pass<float>(g, zmode, mask, s->spec32, nullptr, st));
+    HMG_TRACED(HMG_K_Y_INVERSE, f * 2 * F, launch_y_pass<float>(g, false, mask, s->spec32, st));
+    if (!last) {
+        const bool wtau = b == blk - 2;   // the field the residual sweep compares against
+        const double xb = f * 2 * F + (double)g.N3 + (wtau ? f * F : 0.0) + (addr ? f * F : 0.0);
+        HMG_TRACED(HMG_K_X_ROUND, xb, fast_x_round(g, addr, wtau, mask, s->spec32, s->f32buf, r32in, st));
+        return;
+    }
+    const double xb = f * 3 * F + (addr ? f * F : 0.0);   // spectrum and old field in, field out
+    HMG_TRACED(HMG_K_X_INVERSE, xb,
+               launch_x_inverse<float>(g, ximode, mask, s->spec32, s->f32buf, r32in, nullptr, nullptr, pb, st));
+    HMG_TRACED(HMG_K_OTHER, 0.0, launch_reduce(pb, g.nslots, x_ctas_for<float>(g), 1, s->red + red_off, st));
+}
+
 template <typename R>
 void Solver::equilibrium(unsigned mask, const R* field, void* spec) {
     const double f = (double)popc(mask) * 3.0 * (double)g.N3;
@@ -566,13 +602,8 @@ hmg_status Solver::run_bulk(int max_iter, double tol, hmg_info* info, double K[9
         const int blk = std::max(1, std::min(kResidualEvery, max_iter - total + 1));
         if (ma || mi) {
             for (int b = 0; b < blk; ++b) {
-                const bool last = b == blk - 1;
-                if (ma)
-                    sweep<float>(ma, s->f32buf, s->spec32, Z_ITER, last ? XI_INPLACE_RES : XI_INPLACE, nullptr,
-                                 nullptr, nullptr, 0);
-                if (mi)
-                    sweep<float>(mi, s->f32buf, s->spec32, Z_ITER_NOB, last ? XI_ADD_R_RES : XI_ADD_R, s->r32,
-                                 nullptr, nullptr, 8);
+                if (ma) block_sweep(ma, b, blk, Z_ITER, false, nullptr, 0);
+                if (mi) block_sweep(mi, b, blk, Z_ITER_NOB, true, s->r32, 8);
             }
             cudaMemcpyAsync(h, s->red, 16 * sizeof(double), cudaMemcpyDeviceToHost, st);
             total += blk - 1;

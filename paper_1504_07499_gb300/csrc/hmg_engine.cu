@@ -109,6 +109,7 @@ hmg_status Engine::add(long long id, const uint8_t* phase, int N, const double k
         const int v = autotune_z(ctx, e->g, &e->st, st);
         e->g.zvar = v & 1;
         e->g.xyvar = (v >> 1) & 1;
+        e->g.nochain = (v >> 2) & 1;
     }
     launch_init_tau<float>(e->g, 7u, e->st.f32buf, st);
     e->index = (int)entries.size();
@@ -136,6 +137,25 @@ static void block_launches(const Entry* e, int* dflags, cudaStream_t s) {
     GridDesc gf = e->g;
     gf.dflags = dflags + 4 * e->index;
     SolveState st = e->st;
+    if (chain_sweeps(gf)) {
+        // chained sweeps: x inverse + next x forward in one kernel, the field stored only
+        // before the last sweep (the residual sweep)
+        launch_x_forward<float>(gf, XF_POLARIZE, 7u, st.f32buf, st.spec32, nullptr, s);
+        for (int b = 0; b < kResidualEvery; ++b) {
+            const bool last = b == kResidualEvery - 1;
+            gf.resid = last;
+            launch_y_pass<float>(gf, true, 7u, st.spec32, s);
+            launch_z_pass<float>(gf, Z_ITER, 7u, st.spec32, nullptr, s);
+            launch_y_pass<float>(gf, false, 7u, st.spec32, s);
+            if (!last)
+                fast_x_round(gf, true, b == kResidualEvery - 2, 7u, st.spec32, st.f32buf, st.r32, s);
+            else
+                launch_x_inverse<float>(gf, XI_ADD_R_RES, 7u, st.spec32, st.f32buf, st.r32, nullptr, nullptr,
+                                        st.partial, s);
+        }
+        launch_reduce(st.partial, 3, x_ctas_for<float>(gf), 1, st.red, s);
+        return;
+    }
     for (int b = 0; b < kResidualEvery; ++b) {
         gf.resid = b == kResidualEvery - 1;
         launch_xy_forward<float>(gf, XF_POLARIZE, 7u, st.f32buf, st.spec32, nullptr, s);

@@ -304,8 +304,9 @@ k_fx_forward(GridDesc g, unsigned mask, const float* __restrict__ tau, float2* _
 #pragma unroll
         for (int n1 = 0; n1 < E; ++n1) {
             const uchar2 q = ph[TP * n1 + t];
-            v[n1].x *= sel3f(q.x, c0, c1, c2);
-            v[n1].y *= sel3f(q.y, c0, c1, c2);
+            // rounded products (never contracted into the transform's adds), as in k_fx_round
+            v[n1].x = __fmul_rn(v[n1].x, sel3f(q.x, c0, c1, c2));
+            v[n1].y = __fmul_rn(v[n1].y, sel3f(q.y, c0, c1, c2));
             if (MODE == XF_FLUX) acc += v[n1].x + v[n1].y;
         }
     }
@@ -414,10 +415,7 @@ k_fx_inverse(GridDesc g, unsigned mask, const float2* __restrict__ spec, float* 
 #pragma unroll
     for (int j = 0; j < E; ++j) {
         float2 x = rs[t + TP * j];
-        if (addr) {
-            x.x += radd[j].x;
-            x.y += radd[j].y;
-        }
+        if (addr) x = make_float2(__fadd_rn(x.x, radd[j].x), __fadd_rn(x.y, radd[j].y));
         if (res) {
             const float da = x.x - old[j].x, db = x.y - old[j].y;
             acc += da * da + db * db;
@@ -427,6 +425,113 @@ k_fx_inverse(GridDesc g, unsigned mask, const float2* __restrict__ spec, float* 
     if (kRes) {   // uniform across the CTA (kernel argument and per-slot flag)
         const double s = block_sum_d((double)acc, red);
         if (threadIdx.x == 0 && res) partial[(long long)slot * gridDim.x + blockIdx.x] = s;
+    }
+}
+
+// x inverse of one sweep fused with the polarization and x forward of the next sweep
+// (steps 5-7 of sweep n, steps 2-3 of sweep n + 1) over each row: the updated field
+// tau^{n+1} (plus the defect r in correction sweeps) stays in registers and is written
+// to memory only when WTAU is set (the field a following residual sweep compares
+// against).  The spectrum is transformed in place.  Same float operations as
+// k_fx_inverse followed by k_fx_forward<XF_POLARIZE>, so results are identical.
+template <int M, int RW, bool ADDR, bool WTAU>
+__global__ void __launch_bounds__(RW * Split<M>::TP, 2)
+k_fx_round(GridDesc g, unsigned mask, float2* __restrict__ spec, float* __restrict__ tau,
+           const float* __restrict__ r32) {
+    constexpr int E = Split<M>::E, TP = Split<M>::TP, KPT = E / TP, RS = row_stride<M>();
+    const int slot = blockIdx.y;
+    if (!slot_active(g, mask, slot)) return;
+    extern __shared__ __align__(16) float2 sh[];   // RW * RS
+    const int N = g.N;
+    const int t = threadIdx.x % TP, r = threadIdx.x / TP;
+    // component fastest across CTAs (phase rows reused from L2, as in k_fx_forward)
+    const int comp = blockIdx.x % 3;
+    const long long rblk = blockIdx.x / 3;
+    const long long row = comp * g.NN + rblk * RW + r;              // c*NN + z*N + y
+    const long long fbase = (long long)slot * 3 * g.N3 + row * N;
+    const bool addr = ADDR && (g.dflags ? (g.dflags[slot] & SF_ADDR) != 0 : true);
+    // loads for the update and the polarization: in flight during the inverse FFT
+    float2 radd[E];
+    if (addr) {
+        const float2* rr = reinterpret_cast<const float2*>(r32 + fbase);
+#pragma unroll
+        for (int j = 0; j < E; ++j) radd[j] = rr[t + TP * j];
+    }
+    const uchar2* ph = reinterpret_cast<const uchar2*>(g.phase + (row % g.NN) * N);
+    uchar2 q[E];
+#pragma unroll
+    for (int j = 0; j < E; ++j) q[j] = ph[TP * j + t];
+    float2* sp = spec + (long long)slot * 3 * g.NNM + row * M;
+    float2* rs = sh + r * RS;
+#pragma unroll
+    for (int j = 0; j < E; ++j) rs[t + TP * j] = sp[t + TP * j];
+    __syncthreads();
+    // complex-to-real merge into the stage-1 layout
+    const float2* twN = g.tw32 + g.pN.tw_off;
+    const float2* twM = g.tw32 + g.pM.tw_off;
+    float2 v[E];
+#pragma unroll
+    for (int n1 = 0; n1 < E; ++n1) {
+        const int k = TP * n1 + t;
+        float2 xk, xm;
+        if (k == 0) {
+            const float2 z = rs[0];
+            xk = make_float2(z.x, 0.f);
+            xm = make_float2(z.y, 0.f);
+        } else {
+            xk = rs[k];
+            xm = rs[M - k];
+        }
+        const float2 s = make_float2(xk.x + xm.x, xk.y - xm.y);
+        const float2 d = make_float2(xk.x - xm.x, xk.y + xm.y);
+        const float2 dw = cmulc(d, __ldg(&twN[k]));
+        v[n1] = make_float2(s.x - dw.y, s.y + dw.x);
+    }
+    __syncthreads();
+    stage1_write<M, false>(v, t, twM, rs, 1);
+    __syncthreads();
+    stage2_read<M, false>(v, t, rs, 1);
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < KPT; ++i)
+#pragma unroll
+        for (int k2 = 0; k2 < TP; ++k2) rs[t * KPT + i + E * k2] = v[i * TP + k2];
+    __syncthreads();
+    // update (step 7), optional store, polarization of the next sweep (step 2)
+    const float c0 = (float)g.Y[0], c1 = (float)g.Y[1], c2 = (float)g.Y[2];
+    float2* out = reinterpret_cast<float2*>(tau + fbase);
+#pragma unroll
+    for (int j = 0; j < E; ++j) {
+        float2 x = rs[t + TP * j];
+        if (addr) x = make_float2(__fadd_rn(x.x, radd[j].x), __fadd_rn(x.y, radd[j].y));
+        if (WTAU) out[t + TP * j] = x;
+        v[j] = make_float2(__fmul_rn(x.x, sel3f(q[j].x, c0, c1, c2)), __fmul_rn(x.y, sel3f(q[j].y, c0, c1, c2)));
+    }
+    __syncthreads();   // every thread has read its row values
+    stage1_write<M, true>(v, t, twM, rs, 1);
+    __syncthreads();
+    stage2_read<M, true>(v, t, rs, 1);
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < KPT; ++i)
+#pragma unroll
+        for (int k2 = 0; k2 < TP; ++k2) rs[t * KPT + i + E * k2] = v[i * TP + k2];
+    __syncthreads();
+    // real-to-complex split, written over the row it came from
+#pragma unroll
+    for (int j = 0; j < E; ++j) {
+        const int k = t + TP * j;
+        const float2 z = rs[k];
+        float2 o2;
+        if (k == 0) {
+            o2 = make_float2(z.x + z.y, z.x - z.y);
+        } else {
+            const float2 zm = rs[M - k];
+            const float2 e = make_float2(0.5f * (z.x + zm.x), 0.5f * (z.y - zm.y));
+            const float2 o = make_float2(0.5f * (z.y + zm.y), -0.5f * (z.x - zm.x));
+            o2 = cadd(e, cmul(o, __ldg(&twN[k])));
+        }
+        sp[k] = o2;
     }
 }
 
@@ -597,6 +702,36 @@ bool fast_x_inverse(const GridDesc& g, int mode, unsigned mask, const void* spec
         default: return false;
     }
 #undef FXI
+}
+
+bool chain_sweeps(const GridDesc& g) {
+    return !g.nochain && !(g.xyvar == 1 && fused_cluster(g.N)) && fast_x_ctas(g) > 0;
+}
+
+bool fast_x_round(const GridDesc& g, bool addr, bool wtau, unsigned mask, void* spec, float* tau, const float* r32,
+                  cudaStream_t st) {
+    float2* sp = reinterpret_cast<float2*>(spec);
+    if (!fast_x_ctas(g)) return false;
+#define FXR(M)                                                                                                      \
+    {                                                                                                               \
+        constexpr int RW = fx_rows<M>();                                                                            \
+        constexpr int T = RW * fast::Split<M>::TP;                                                                  \
+        dim3 grid(fast_x_ctas(g), g.nslots);                                                                        \
+        const size_t sm = sizeof(float2) * RW * fast::row_stride<M>();                                              \
+        if (addr && wtau) launch_dyn(fast::k_fx_round<M, RW, true, true>, grid, T, sm, st, g, mask, sp, tau, r32);   \
+        else if (addr) launch_dyn(fast::k_fx_round<M, RW, true, false>, grid, T, sm, st, g, mask, sp, tau, r32);     \
+        else if (wtau) launch_dyn(fast::k_fx_round<M, RW, false, true>, grid, T, sm, st, g, mask, sp, tau, r32);     \
+        else launch_dyn(fast::k_fx_round<M, RW, false, false>, grid, T, sm, st, g, mask, sp, tau, r32);              \
+    }
+    switch (g.M) {
+        HMG_FAST_LEN(32, FXR)
+        HMG_FAST_LEN(48, FXR)
+        HMG_FAST_LEN(64, FXR)
+        HMG_FAST_LEN(96, FXR)
+        HMG_FAST_LEN(128, FXR)
+        default: return false;
+    }
+#undef FXR
 }
 
 #undef HMG_FAST_LEN

@@ -38,6 +38,12 @@ template <bool FWD, typename T2> __device__ __forceinline__ T2 mul_mi(T2 a) {
     return FWD ? mk(a.y, -a.x) : mk(-a.y, a.x);
 }
 
+// FP32 complex adds and subtracts as single packed two-lane FP32 instructions (sm_100
+// and later); a - b is b * (-1) + a, exact product, one rounding, as the scalar form.
+// Overloads of the templates above, chosen for float2.
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+
 template <typename T2> struct TwTable;
 template <> struct TwTable<float2> {
     static __device__ __forceinline__ const float2* get(const GridDesc& g) { return g.tw32; }

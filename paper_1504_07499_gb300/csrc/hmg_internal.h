@@ -39,6 +39,7 @@ struct GridDesc {
     int Py, Pz;            // columns per CTA in the y and z passes
     int zvar;              // z-pass kernel variant of the register-resident path (autotuned)
     int xyvar;             // 1: fused x + y cluster kernels, 0: separate x and y passes (autotuned)
+    int nochain;           // 1: FP32 sweeps of a block are not chained through k_fx_round
     // Per-slot flags in device memory (engine launches; nullptr = use the launch's
     // mask and template modes): SF_ACTIVE, SF_ADDB (add 2 k0 E at DC, plain sweep),
     // SF_ADDR (add the defect r, correction sweep).  `resid`: this launch of the x
@@ -93,6 +94,13 @@ bool fast_x_forward(const GridDesc& g, int mode, unsigned mask, const float* tau
                     cudaStream_t st);
 bool fast_x_inverse(const GridDesc& g, int mode, unsigned mask, const void* spec, float* tau, const float* r32,
                     double* partial, cudaStream_t st);
+// x inverse of a sweep + polarization and x forward of the next, in place on the
+// spectrum; adds r (addr; per-slot flag in flags mode) and stores the updated field (wtau).
+bool fast_x_round(const GridDesc& g, bool addr, bool wtau, unsigned mask, void* spec, float* tau, const float* r32,
+                  cudaStream_t st);
+// FP32 sweeps of a block are chained (x inverse + next x forward in one kernel):
+// register-resident x kernels exist for g.N, separate x and y passes, chaining not off.
+bool chain_sweeps(const GridDesc& g);
 int fast_x_ctas(const GridDesc& g);
 int fast_z_ctas(const GridDesc& g);
 

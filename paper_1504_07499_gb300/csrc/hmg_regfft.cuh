@@ -43,6 +43,17 @@ __device__ __forceinline__ float2 wE(int m) {
     return FWD ? make_float2(c, -s) : make_float2(c, s);
 }
 
+// x * w_E^m with the quarter turns (w = -1, +-i) done exactly by swaps and signs.
+template <int E, bool FWD>
+__device__ __forceinline__ float2 twiddle_E(float2 x, int m) {
+    const int q = (m * 4) % E == 0 ? (m * 4 / E) % 4 : -1;   // m a multiple of E/4: quarter turns
+    if (q == 0) return x;
+    if (q == 2) return make_float2(-x.x, -x.y);
+    if (q == 1) return FWD ? make_float2(x.y, -x.x) : make_float2(-x.y, x.x);   // w = -i (forward)
+    if (q == 3) return FWD ? make_float2(-x.y, x.x) : make_float2(x.y, -x.x);
+    return cmul(x, wE<E, FWD>(m));
+}
+
 // Length-E DFT in registers, natural order in and out.
 template <int E, bool FWD>
 struct RegDFT {
@@ -59,7 +70,7 @@ struct RegDFT {
 #pragma unroll
         for (int a = 1; a < A; ++a)
 #pragma unroll
-            for (int k = 1; k < B; ++k) s[a][k] = cmul(s[a][k], wE<E, FWD>(a * k));
+            for (int k = 1; k < B; ++k) s[a][k] = twiddle_E<E, FWD>(s[a][k], a * k);
 #pragma unroll
         for (int k = 0; k < B; ++k) {
             float2 t[A];

@@ -101,6 +101,13 @@ struct Solver {
     template <typename R>
     void sweep(unsigned mask, R* field, void* spec, int zmode, int ximode, const float* r32in, float* d32,
                float* r32out, int red_off = 0);
+    // Sweep b of a block of blk FP32 sweeps on f32buf / spec32 (plain: Z_ITER without r;
+    // correction: Z_ITER_NOB with r added).  Where the register-resident x kernels exist
+    // the sweeps of a block are chained: the x inverse of sweep b and the x forward of
+    // sweep b + 1 are one kernel and the field goes to memory only before the last sweep,
+    // whose x inverse computes the residual (left at red[red_off + slot]).
+    void block_sweep(unsigned mask, int b, int blk, int zmode, bool addr, const float* r32in, int red_off);
+    bool chained() const;
     template <typename R>
     void equilibrium(unsigned mask, const R* field, void* spec);
     template <typename R>

@@ -32,7 +32,8 @@ EXPORTS = ["hmg_version", "hmg_last_error", "hmg_create", "hmg_destroy", "hmg_vo
            "hmg_trace_read", "hmg_equilibrium_noalloc", "hmg_set_variant", "hmg_get_variant",
            "hmg_server_stats"]
 HMG_NOALLOC_MAX_N = 64
-KERNEL_KINDS = ["x_forward", "y_forward", "z_green", "y_inverse", "x_inverse", "eq_x", "eq_z", "other"]
+KERNEL_KINDS = ["x_forward", "y_forward", "z_green", "y_inverse", "x_inverse", "eq_x", "eq_z", "other",
+                "x_round"]
 
 
 class hmg_sphere(C.Structure):

@@ -119,3 +119,40 @@ def test_autotuner_records_a_variant(ctx):
     e[0] = 1.0
     hmg.hmg_em_iterate(ctx.handle, ph, N, K3, (1.0, 0.0, 0.0), hmg.HMG_FP32_BULK, 1, e)
     assert hmg.hmg_get_variant(ctx.handle, N) in (0, 1, 2, 3)
+
+
+@pytest.mark.parametrize("N", [64, 96, 128])
+def test_chained_sweeps_are_bit_identical(ctx, N):
+    """Chained FP32 sweeps (variant bit 2 clear: x inverse + next x forward in one kernel)
+    against unchained ones (bit 2 set): the same K, sweep counts and fields, bit for bit."""
+    sl = I.generate_spheres(1000, 30, 0.2)
+    ph = om.voxelize(sl.spheres, 0.3, N)
+    k = (0.20, 0.25, 40.0)
+    out = []
+    for v in (0, 4):
+        hmg.hmg_set_variant(ctx.handle, N, v)
+        e = np.empty((3, 3, N, N, N))
+        K, info, st = hmg.hmg_solve_fields(ctx.handle, ph, N, k, 1e-8, hmg.HMG_FP32_BULK, e)
+        assert st == hmg.HMG_OK
+        out.append((K, info, e))
+    hmg.hmg_set_variant(ctx.handle, N, -1)
+    assert np.array_equal(out[0][0], out[1][0])
+    assert list(out[0][1]["iters"]) == list(out[1][1]["iters"])
+    assert np.array_equal(out[0][2], out[1][2])
+
+
+def test_chained_engine_batch_is_bit_identical(ctx):
+    """The engine's graph of chained blocks against unchained blocks (hmg_solve_batch)."""
+    N = 64
+    phs = [om.voxelize(I.generate_spheres(s, 20, 0.3).spheres, 0.3, N) for s in (11, 12)]
+    res = []
+    for v in (0, 4):
+        hmg.hmg_set_variant(ctx.handle, N, v)
+        K, infos, st = hmg.hmg_solve_batch(ctx.handle, phs, [N, N], np.array([I.K_PHASES, (0.2, 0.25, 40.0)]),
+                                           1e-8, hmg.HMG_FP32_BULK)
+        assert st == hmg.HMG_OK
+        res.append((K, infos))
+    hmg.hmg_set_variant(ctx.handle, N, -1)
+    assert np.array_equal(res[0][0], res[1][0])
+    for a, b in zip(res[0][1], res[1][1]):
+        assert list(a["iters"]) == list(b["iters"])
