@@ -166,9 +166,10 @@ def main() -> None:
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison solve")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
-    ap.add_argument("--mode", default="single", choices=["single", "batch", "serve"],
+    ap.add_argument("--mode", default="single", choices=["single", "batch", "serve", "contrast"],
                     help="single: the 256^3 RVE (default); batch: 64 mixed-size RVEs in one engine; "
-                         "serve: Poisson request stream through hmg_submit/hmg_poll")
+                         "serve: Poisson request stream through hmg_submit/hmg_poll; "
+                         "contrast: the 256^3 RVE over 4 contrasts x 3 layers, FP32 bulk and FP64")
     ap.add_argument("--requests", type=int, default=48, help="serve mode: requests per arrival rate")
     ap.add_argument("--variant", type=int, default=-1,
                     help="pin the FP32 kernel variant of the 256^3 grid (0..7, see hmg_set_variant); "
@@ -181,6 +182,9 @@ def main() -> None:
         return
     if args.mode == "batch":
         run_batch(args)
+        return
+    if args.mode == "contrast":
+        run_contrast(args)
         return
     if args.mode == "serve":
         run_serve(args)
@@ -305,7 +309,9 @@ def main() -> None:
         peak = 6800.0
     kinds = {k: v for k, v in trace.items() if v[1] > 0}
     total_ms = sum(v[0] for v in kinds.values())
-    dom = max((k for k in kinds if k != "other"), key=lambda k: kinds[k][0])
+    # the dominant kernel of the solve's own precision (FP64 correction passes are one kind)
+    skip = ("other", "fp64") if args.precision == "fp32bulk" else ("other",)
+    dom = max((k for k in kinds if k not in skip), key=lambda k: kinds[k][0])
     d_ms, d_n, d_bytes = kinds[dom]
     achieved = (d_bytes / d_n) / (d_ms / d_n / 1e3) / 1e9
     traffic = None
@@ -440,6 +446,73 @@ def run_batch(args) -> None:
             "plain_fp64_estimate": {"seconds": est_fp64_s, "per_size": fp64, "batch_speedup": est_fp64_s / dt},
             "mean_K_trace_over_3": kbar,
             "status_all_ok": bool(st == hmg.HMG_OK)}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+
+
+def run_contrast(args) -> None:
+    """Contrast and layer sweep on the 256^3 RVE (100 spheres at 40 %, seed 3000): l in
+    {0.1, 0.3, 0.5} x k_coat in {2, 40, 400, 4000} (contrast 10 .. 2e4 with k_min = 0.2),
+    each solved in FP32 bulk and in plain FP64 to tol 1e-8.  Reports sweeps per gradient
+    against the contraction bound ln(tol)/ln(rho), rho = (sqrt(c)-1)/(sqrt(c)+1), the
+    throughput of both forms, the dominant FP32 kernel's bandwidth from the tracer and the
+    two forms' K difference."""
+    import torch
+    from paper_1504_07499_gb300 import build, hmg
+    from paper_1504_07499_gb300 import inputs as I
+    build.build()
+    ctx = hmg.Context(0)
+    sl = I.generate_spheres(SEED, N_SPHERES, F_SP)
+    sph_d = torch.from_numpy(np.ascontiguousarray(sl.spheres)).cuda()
+    N = N_GRID
+    peak = measured_peaks().get("hbm_gbs") or 6800.0
+    ph = torch.empty(N ** 3, dtype=torch.uint8, device="cuda")
+    hmg.hmg_voxelize(ctx.handle, sph_d, 0.3, N, ph)
+    hmg.hmg_solve(ctx.handle, ph, N, K_PHASES, TOL, hmg.HMG_FP32_BULK)     # autotune + warm-up
+    cases, vox32, t32, vox64, t64 = [], 0.0, 0.0, 0.0, 0.0
+    for layer in (0.1, 0.3, 0.5):
+        hmg.hmg_voxelize(ctx.handle, sph_d, layer, N, ph)
+        for kc in (2.0, 40.0, 400.0, 4000.0):
+            k = (K_PHASES[0], K_PHASES[1], kc)
+            c = max(k) / min(k)
+            rho = (np.sqrt(c) - 1) / (np.sqrt(c) + 1)
+            row = {"layer": layer, "k_coat": kc, "contrast": c, "bound_sweeps": float(np.log(TOL) / np.log(rho))}
+            for name, prec in (("fp32bulk", hmg.HMG_FP32_BULK), ("fp64", hmg.HMG_FP64)):
+                hmg.hmg_trace_enable(ctx.handle, True)
+                torch.cuda.synchronize()
+                t = time.perf_counter()
+                K, info, st = hmg.hmg_solve(ctx.handle, ph, N, k, TOL, prec, allow=(hmg.HMG_OK, hmg.HMG_NOT_CONVERGED))
+                dt = time.perf_counter() - t
+                tr = hmg.hmg_trace_read(ctx.handle)
+                hmg.hmg_trace_enable(ctx.handle, False)
+                sweeps = int(sum(info["iters"]))
+                ent = {"status": int(st), "sweeps_per_gradient": list(info["iters"]), "solve_s": dt,
+                       "voxel_iter_per_s": N ** 3 * sweeps / dt, "K": K.tolist(),
+                       "algorithmic_hbm_frac": N ** 3 * sweeps / dt * (25.0 if name == "fp32bulk" else 49.0) / 1e9 / peak}
+                if name == "fp32bulk":
+                    kinds = {kk: v for kk, v in tr.items() if v[1] > 0 and kk not in ("other", "fp64")}
+                    dom = max(kinds, key=lambda kk: kinds[kk][0])
+                    ms, n, b = kinds[dom]
+                    ent["dominant_kernel"] = {"kind": dom, "GBps": b / (ms / 1e3) / 1e9, "frac": b / (ms / 1e3) / 1e9 / peak}
+                    ent["fp64_rounds"] = int(info.get("fp64_rounds", 0))
+                    vox32 += N ** 3 * sweeps
+                    t32 += dt
+                else:
+                    vox64 += N ** 3 * sweeps
+                    t64 += dt
+                row[name] = ent
+            K32, K64 = np.array(row["fp32bulk"]["K"]), np.array(row["fp64"]["K"])
+            row["K_rel_diff"] = float(np.abs(K32 - K64).max() / np.abs(K64).max())
+            cases.append(row)
+            print(json.dumps({"case": row}), file=sys.stderr, flush=True)
+    line = {"metric": "voxel-iterations/s at 256^3 over contrast 10..2e4 and layer 0.1..0.5 (3 unit gradients, tol 1e-8)",
+            "value": vox32 / t32, "unit": UNIT, "n_gpus": 1, "steps": len(cases), "warmup": 1,
+            "ms_per_step": 1e3 * t32 / len(cases), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "rsa256 contrast sweep: 256^3, 100 spheres at 40 % (seed 3000), l in {0.1,0.3,0.5}, "
+                                   "k 0.20/0.25/{2,40,400,4000}", "precision": "fp32bulk"},
+            "fp64_plain": {"voxel_iter_per_s": vox64 / t64, "seconds": t64, "speedup_fp32bulk": t64 / t32},
+            "cases": cases}
     print(json.dumps(line), flush=True)
     ctx.close()
 

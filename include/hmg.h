@@ -252,7 +252,8 @@ typedef enum {
     HMG_K_OTHER = 7,       /* reductions, conversions, voxelization */
     HMG_K_X_ROUND = 8,     /* x pass inverse + update of one sweep fused with the
                               polarization + x pass forward of the next (steps 5-7, 2-3) */
-    HMG_K_COUNT = 9
+    HMG_K_FP64 = 9,        /* every pass of an FP64 sweep or FP64 equilibrium test */
+    HMG_K_COUNT = 10
 } hmg_kernel_kind;
 
 /* Start (enable = 1, counters reset) or stop (0) timing every kernel the solver

@@ -388,6 +388,12 @@ static int popc(unsigned m) { return __builtin_popcount(m); }
         if (tr) tr->end(ev_, KIND, BYTES, st); \
     } while (0)
 
+// FP64 launches are traced as one kind of their own.
+template <typename R>
+static constexpr int kind_of(int k) {
+    return std::is_same<R, double>::value ? HMG_K_FP64 : k;
+}
+
 template <typename R>
 void Solver::sweep(unsigned mask, R* field, void* spec, int zmode, int ximode, const float* r32in,
                    float* d32, float* r32out, int red_off) {
@@ -402,22 +408,22 @@ void Solver::sweep(unsigned mask, R* field, void* spec, int zmode, int ximode, c
     if (ximode == XI_DIFF) xb = f * F + f * F + 2 * f * 4;      // spectrum, old field, d and r out
     if (fused) {
         // x+y forward and y+x inverse: one cluster kernel each
-        HMG_TRACED(HMG_K_X_FORWARD, f * 2 * F + (double)g.N3,
+        HMG_TRACED(kind_of<R>(HMG_K_X_FORWARD), f * 2 * F + (double)g.N3,
                    launch_xy_forward<R>(g, XF_POLARIZE, mask, field, spec, nullptr, st));
-        HMG_TRACED(HMG_K_Z_GREEN, f * 2 * F, launch_z_pass<R>(g, zmode, mask, spec, nullptr, st));
-        HMG_TRACED(HMG_K_X_INVERSE, xb,
+        HMG_TRACED(kind_of<R>(HMG_K_Z_GREEN), f * 2 * F, launch_z_pass<R>(g, zmode, mask, spec, nullptr, st));
+        HMG_TRACED(kind_of<R>(HMG_K_X_INVERSE), xb,
                    launch_yx_inverse<R>(g, ximode, mask, spec, field, r32in, d32, r32out, pb, st));
     } else {
-        HMG_TRACED(HMG_K_X_FORWARD, f * 2 * F + (double)g.N3,
+        HMG_TRACED(kind_of<R>(HMG_K_X_FORWARD), f * 2 * F + (double)g.N3,
                    launch_x_forward<R>(g, XF_POLARIZE, mask, field, spec, nullptr, st));
-        HMG_TRACED(HMG_K_Y_FORWARD, f * 2 * F, launch_y_pass<R>(g, true, mask, spec, st));
-        HMG_TRACED(HMG_K_Z_GREEN, f * 2 * F, launch_z_pass<R>(g, zmode, mask, spec, nullptr, st));
-        HMG_TRACED(HMG_K_Y_INVERSE, f * 2 * F, launch_y_pass<R>(g, false, mask, spec, st));
-        HMG_TRACED(HMG_K_X_INVERSE, xb,
+        HMG_TRACED(kind_of<R>(HMG_K_Y_FORWARD), f * 2 * F, launch_y_pass<R>(g, true, mask, spec, st));
+        HMG_TRACED(kind_of<R>(HMG_K_Z_GREEN), f * 2 * F, launch_z_pass<R>(g, zmode, mask, spec, nullptr, st));
+        HMG_TRACED(kind_of<R>(HMG_K_Y_INVERSE), f * 2 * F, launch_y_pass<R>(g, false, mask, spec, st));
+        HMG_TRACED(kind_of<R>(HMG_K_X_INVERSE), xb,
                    launch_x_inverse<R>(g, ximode, mask, spec, field, r32in, d32, r32out, pb, st));
     }
     if (ximode == XI_INPLACE_RES || ximode == XI_ADD_R_RES || ximode == XI_DIFF)
-        HMG_TRACED(HMG_K_OTHER, 0.0, launch_reduce(pb, g.nslots, x_ctas_for<R>(g), 1, s->red + red_off, st));
+        HMG_TRACED(kind_of<R>(HMG_K_OTHER), 0.0, launch_reduce(pb, g.nslots, x_ctas_for<R>(g), 1, s->red + red_off, st));
 }
 
 bool Solver::chained() const { return chain_sweeps(g); }
@@ -457,14 +463,14 @@ void Solver::equilibrium(unsigned mask, const R* field, void* spec) {
     const bool fused = std::is_same<R, float>::value && g.xyvar == 1 && fused_cluster(g.N) != 0;
     double* pb = pflux ? pflux : s->partial;
     if (fused) {
-        HMG_TRACED(HMG_K_EQ_X, f * 2 * F + (double)g.N3, launch_xy_forward<R>(g, XF_FLUX, mask, field, spec, pb, st));
+        HMG_TRACED(kind_of<R>(HMG_K_EQ_X), f * 2 * F + (double)g.N3, launch_xy_forward<R>(g, XF_FLUX, mask, field, spec, pb, st));
     } else {
-        HMG_TRACED(HMG_K_EQ_X, f * 2 * F + (double)g.N3, launch_x_forward<R>(g, XF_FLUX, mask, field, spec, pb, st));
+        HMG_TRACED(kind_of<R>(HMG_K_EQ_X), f * 2 * F + (double)g.N3, launch_x_forward<R>(g, XF_FLUX, mask, field, spec, pb, st));
     }
-    HMG_TRACED(HMG_K_OTHER, 0.0, launch_reduce(pb, g.nslots, x_ctas_for<R>(g), 3, s->red + 16, st));
-    if (!fused) HMG_TRACED(HMG_K_Y_FORWARD, f * 2 * F, launch_y_pass<R>(g, true, mask, spec, st));
-    HMG_TRACED(HMG_K_EQ_Z, f * F, launch_z_pass<R>(g, Z_EQ, mask, spec, s->partial2, st));
-    HMG_TRACED(HMG_K_OTHER, 0.0, launch_reduce(s->partial2, g.nslots, z_ctas_for<R>(g), 1, s->red + 32, st));
+    HMG_TRACED(kind_of<R>(HMG_K_OTHER), 0.0, launch_reduce(pb, g.nslots, x_ctas_for<R>(g), 3, s->red + 16, st));
+    if (!fused) HMG_TRACED(kind_of<R>(HMG_K_Y_FORWARD), f * 2 * F, launch_y_pass<R>(g, true, mask, spec, st));
+    HMG_TRACED(kind_of<R>(HMG_K_EQ_Z), f * F, launch_z_pass<R>(g, Z_EQ, mask, spec, s->partial2, st));
+    HMG_TRACED(kind_of<R>(HMG_K_OTHER), 0.0, launch_reduce(s->partial2, g.nslots, z_ctas_for<R>(g), 1, s->red + 32, st));
 }
 
 bool Solver::fetch(double* h, int off, int count) {

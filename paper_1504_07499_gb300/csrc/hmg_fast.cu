@@ -274,15 +274,143 @@ k_fzs(GridDesc g, unsigned mask, float2* __restrict__ spec, double* __restrict__
 // x passes: R rows per CTA, threads (t, r) with t fastest along the row
 // ---------------------------------------------------------------------------
 
+// Real-to-complex split of one row whose M-point transform Z is in natural order in rs:
+// X[k] = e + o w_N^k with e = (Z[k] + conj Z[M-k]) / 2 and o = -i (Z[k] - conj Z[M-k]) / 2,
+// and X[M-k] = conj(e - o w_N^k) (w_N^(M-k) = -conj w_N^k); X[0] packs X(0) and X(N/2),
+// X[M/2] = conj Z[M/2].  Thread t of the row writes the pairs k = t + TP j, j < E/2.
+// twN: w_N^k, k < M, staged in shared memory.
+template <int M, int TP, int E>
+__device__ __forceinline__ void r2c_split_store(const float2* rs, const float2* __restrict__ twN,
+                                                float2* __restrict__ dst, int t) {
+#pragma unroll
+    for (int j = 0; j < E / 2; ++j) {
+        const int k = t + TP * j;
+        const float2 z = rs[k];
+        if (k == 0) {
+            dst[0] = make_float2(z.x + z.y, z.x - z.y);
+            const float2 h = rs[M / 2];
+            dst[M / 2] = make_float2(h.x, -h.y);
+        } else {
+            const float2 zm = rs[M - k];
+            const float2 e = make_float2(0.5f * (z.x + zm.x), 0.5f * (z.y - zm.y));
+            const float2 o = make_float2(0.5f * (z.y + zm.y), -0.5f * (z.x - zm.x));
+            const float2 p = cmul(o, twN[k]);
+            dst[k] = cadd(e, p);
+            const float2 q = csub(e, p);
+            dst[M - k] = make_float2(q.x, -q.y);
+        }
+    }
+}
+
+// Coefficient pairs for two neighbouring voxels of phases (a, b): lut[a | b << 2] = (c_a, c_b).
+__device__ __forceinline__ void coef_pairs(float2* lut, float c0, float c1, float c2) {
+    if (threadIdx.x < 16) {
+        const int a = threadIdx.x & 3, b = threadIdx.x >> 2;
+        const float ca = a == 0 ? c0 : (a == 1 ? c1 : (a == 2 ? c2 : 0.f));
+        const float cb = b == 0 ? c0 : (b == 1 ? c1 : (b == 2 ? c2 : 0.f));
+        lut[threadIdx.x] = make_float2(ca, cb);
+    }
+}
+__device__ __forceinline__ int pair_index(uchar2 q) { return q.x | (q.y << 2); }
+
+// Stage the x pass twiddles in shared memory: tws[k] = w_M^k, tws[M + k] = w_N^k (k < M).
+// Read after the caller's next barrier.
+template <int M>
+__device__ __forceinline__ void stage_twiddles(float2* tws, const GridDesc& g) {
+    const float2* twM = g.tw32 + g.pM.tw_off;
+    const float2* twN = g.tw32 + g.pN.tw_off;
+    for (int i = threadIdx.x; i < 2 * M; i += blockDim.x) tws[i] = i < M ? __ldg(&twM[i]) : __ldg(&twN[i - M]);
+}
+
+// Row values in the stage-2 layout: thread t holds complex position p = (t KPT + i) + E m
+// at v[i TP + m].  With KPT even, positions t KPT + i (i even) are 16-byte aligned pairs,
+// loaded and stored as float4 (and their phase ids as one uchar4).
+template <int M>
+__device__ __forceinline__ void s2_load(float2* v, const float2* __restrict__ row, int t) {
+    constexpr int E = Split<M>::E, TP = Split<M>::TP, KPT = E / TP;
+    if constexpr (KPT % 2 == 0) {
+        const float4* r4 = reinterpret_cast<const float4*>(row);
+#pragma unroll
+        for (int m = 0; m < TP; ++m)
+#pragma unroll
+            for (int i = 0; i < KPT; i += 2) {
+                const float4 q = r4[(t * KPT + i + E * m) / 2];
+                v[i * TP + m] = make_float2(q.x, q.y);
+                v[(i + 1) * TP + m] = make_float2(q.z, q.w);
+            }
+    } else {
+#pragma unroll
+        for (int m = 0; m < TP; ++m)
+#pragma unroll
+            for (int i = 0; i < KPT; ++i) v[i * TP + m] = row[t * KPT + i + E * m];
+    }
+}
+template <int M>
+__device__ __forceinline__ void s2_store(float2* __restrict__ row, const float2* v, int t) {
+    constexpr int E = Split<M>::E, TP = Split<M>::TP, KPT = E / TP;
+    if constexpr (KPT % 2 == 0) {
+        float4* r4 = reinterpret_cast<float4*>(row);
+#pragma unroll
+        for (int m = 0; m < TP; ++m)
+#pragma unroll
+            for (int i = 0; i < KPT; i += 2) {
+                const float2 a = v[i * TP + m], b = v[(i + 1) * TP + m];
+                r4[(t * KPT + i + E * m) / 2] = make_float4(a.x, a.y, b.x, b.y);
+            }
+    } else {
+#pragma unroll
+        for (int m = 0; m < TP; ++m)
+#pragma unroll
+            for (int i = 0; i < KPT; ++i) row[t * KPT + i + E * m] = v[i * TP + m];
+    }
+}
+template <int M>
+__device__ __forceinline__ void s2_load_phase(uchar2* q, const uchar2* __restrict__ row, int t) {
+    constexpr int E = Split<M>::E, TP = Split<M>::TP, KPT = E / TP;
+    if constexpr (KPT % 2 == 0) {
+        const uchar4* r4 = reinterpret_cast<const uchar4*>(row);
+#pragma unroll
+        for (int m = 0; m < TP; ++m)
+#pragma unroll
+            for (int i = 0; i < KPT; i += 2) {
+                const uchar4 b = r4[(t * KPT + i + E * m) / 2];
+                q[i * TP + m] = make_uchar2(b.x, b.y);
+                q[(i + 1) * TP + m] = make_uchar2(b.z, b.w);
+            }
+    } else {
+#pragma unroll
+        for (int m = 0; m < TP; ++m)
+#pragma unroll
+            for (int i = 0; i < KPT; ++i) q[i * TP + m] = row[t * KPT + i + E * m];
+    }
+}
+
+// Forward x transform of a row held in the stage-2 layout, ending with the real split
+// written to dst: decimation-in-frequency stages, the natural-order exchange, the split.
+// Leaves the CTA synchronized on shared memory before the split.
+template <int M, int TP, int E>
+__device__ __forceinline__ void row_forward_split(float2* v, int t, float2* rs, const float2* __restrict__ twM,
+                                                  const float2* __restrict__ twN, float2* __restrict__ dst) {
+    rstage2_write<M, true, true>(v, t, twM, rs, 1);
+    __syncthreads();
+    rstage1_read<M, true>(v, t, rs, 1);   // v[kb] = Z[t + TP kb]
+    __syncthreads();
+#pragma unroll
+    for (int kb = 0; kb < E; ++kb) rs[t + TP * kb] = v[kb];
+    __syncthreads();
+    r2c_split_store<M, TP, E>(rs, twN, dst, t);
+}
+
 template <int M, int RW, int MODE>
 __global__ void __launch_bounds__(RW * Split<M>::TP, 4)
 k_fx_forward(GridDesc g, unsigned mask, const float* __restrict__ tau, float2* __restrict__ spec,
              double* __restrict__ partial) {
-    constexpr int E = Split<M>::E, TP = Split<M>::TP, KPT = E / TP, RS = row_stride<M>();
+    constexpr int E = Split<M>::E, TP = Split<M>::TP, RS = row_stride<M>();
     const int slot = blockIdx.y;
     if (!slot_active(g, mask, slot)) return;
     extern __shared__ __align__(16) float2 sh[];   // RW * RS
     __shared__ double red[RW * TP];
+    __shared__ float2 lut[16];
     const int N = g.N;
     const int t = threadIdx.x % TP, r = threadIdx.x / TP;
     // component fastest across CTAs, so the three components of a (z, y) block read the
@@ -292,65 +420,79 @@ k_fx_forward(GridDesc g, unsigned mask, const float* __restrict__ tau, float2* _
     const long long row = comp * g.NN + rblk * RW + r;              // c*NN + z*N + y
     const long long pidx = comp * (g.NN / RW) + rblk;               // component-major CTA index
     const float2* src = reinterpret_cast<const float2*>(tau + (long long)slot * 3 * g.N3 + row * N);
-    const uchar2* ph = reinterpret_cast<const uchar2*>(g.phase + (row % g.NN) * N);
+    __shared__ float2 tws[2 * M];
+    stage_twiddles<M>(tws, g);
+    if (MODE != XF_PLAIN)
+        coef_pairs(lut, (float)(MODE == XF_POLARIZE ? g.Y[0] : g.W[0]), (float)(MODE == XF_POLARIZE ? g.Y[1] : g.W[1]),
+                   (float)(MODE == XF_POLARIZE ? g.Y[2] : g.W[2]));
+    __syncthreads();
     float2 v[E];
-#pragma unroll
-    for (int n1 = 0; n1 < E; ++n1) v[n1] = src[TP * n1 + t];
+    s2_load<M>(v, src, t);
     float acc = 0.f;
     if (MODE != XF_PLAIN) {
-        const float c0 = (float)(MODE == XF_POLARIZE ? g.Y[0] : g.W[0]);
-        const float c1 = (float)(MODE == XF_POLARIZE ? g.Y[1] : g.W[1]);
-        const float c2 = (float)(MODE == XF_POLARIZE ? g.Y[2] : g.W[2]);
+        uchar2 q[E];
+        s2_load_phase<M>(q, reinterpret_cast<const uchar2*>(g.phase + (row % g.NN) * N), t);
 #pragma unroll
-        for (int n1 = 0; n1 < E; ++n1) {
-            const uchar2 q = ph[TP * n1 + t];
+        for (int j = 0; j < E; ++j) {
             // rounded products (never contracted into the transform's adds), as in k_fx_round
-            v[n1].x = __fmul_rn(v[n1].x, sel3f(q.x, c0, c1, c2));
-            v[n1].y = __fmul_rn(v[n1].y, sel3f(q.y, c0, c1, c2));
-            if (MODE == XF_FLUX) acc += v[n1].x + v[n1].y;
+            v[j] = __fmul2_rn(v[j], lut[pair_index(q[j])]);
+            if (MODE == XF_FLUX) acc += v[j].x + v[j].y;
         }
     }
-    const float2* twM = g.tw32 + g.pM.tw_off;
-    float2* rs = sh + r * RS;
-    stage1_write<M, true>(v, t, twM, rs, 1);
-    __syncthreads();
-    stage2_read<M, true>(v, t, rs, 1);
-    __syncthreads();
-    // natural order into shared memory for the real split
-#pragma unroll
-    for (int i = 0; i < KPT; ++i)
-#pragma unroll
-        for (int k2 = 0; k2 < TP; ++k2) rs[t * KPT + i + E * k2] = v[i * TP + k2];
     if (MODE == XF_FLUX) {
         const double s = block_sum_d((double)acc, red);
         if (threadIdx.x == 0) partial[(long long)slot * gridDim.x + pidx] = s;
-    } else {
-        __syncthreads();
     }
-    const float2* twN = g.tw32 + g.pN.tw_off;
-    float2* dst = spec + (long long)slot * 3 * g.NNM + row * M;
+    row_forward_split<M, TP, E>(v, t, sh + r * RS, tws, tws + M, spec + (long long)slot * 3 * g.NNM + row * M);
+}
+
+// Complex-to-real merge of a row spectrum (natural order in rs) into the stage-1 layout
+// v[n1] = x-transform input at k = TP n1 + t.  twN: w_N^k, k < M, in shared memory.
+template <int M, int TP, int E>
+__device__ __forceinline__ void c2r_merge(float2* v, const float2* rs, const float2* __restrict__ twN, int t) {
 #pragma unroll
-    for (int j = 0; j < E; ++j) {
-        const int k = t + TP * j;
-        const float2 z = rs[k];
-        float2 out;
+    for (int n1 = 0; n1 < E; ++n1) {
+        const int k = TP * n1 + t;
+        float2 xk, xm;
         if (k == 0) {
-            out = make_float2(z.x + z.y, z.x - z.y);
+            const float2 q = rs[0];
+            xk = make_float2(q.x, 0.f);
+            xm = make_float2(q.y, 0.f);
         } else {
-            const float2 zm = rs[M - k];
-            const float2 e = make_float2(0.5f * (z.x + zm.x), 0.5f * (z.y - zm.y));
-            const float2 o = make_float2(0.5f * (z.y + zm.y), -0.5f * (z.x - zm.x));
-            out = cadd(e, cmul(o, __ldg(&twN[k])));
+            xk = rs[k];
+            xm = rs[M - k];
         }
-        dst[k] = out;
+        const float2 s = make_float2(xk.x + xm.x, xk.y - xm.y);
+        const float2 d = make_float2(xk.x - xm.x, xk.y + xm.y);
+        const float2 dw = cmulc(d, twN[k]);
+        v[n1] = make_float2(s.x - dw.y, s.y + dw.x);
     }
 }
 
+// Inverse x transform of a row spectrum: load, merge, stage 1, exchange, stage 2; leaves
+// v in the stage-2 layout (v[i TP + m] = x[(t KPT + i) + E m]).
+template <int M, int TP, int E>
+__device__ __forceinline__ void row_inverse(float2* v, int t, float2* rs, const float2* __restrict__ src,
+                                            const float2* __restrict__ twM, const float2* __restrict__ twN) {
+#pragma unroll
+    for (int j = 0; j < E; ++j) rs[t + TP * j] = src[t + TP * j];
+    __syncthreads();
+    c2r_merge<M, TP, E>(v, rs, twN, t);
+    __syncthreads();
+    stage1_write<M, false, true>(v, t, twM, rs, 1);
+    __syncthreads();
+    stage2_read<M, false>(v, t, rs, 1);
+}
+
+// residual sweeps that also add r hold three row fields in registers: two CTAs per SM
+template <int M, int MODE>
+constexpr int fx_inverse_min_ctas() { return (MODE == XI_ADD_R_RES || Split<M>::E > 16) ? 2 : 3; }
+
 template <int M, int RW, int MODE>
-__global__ void __launch_bounds__(RW * Split<M>::TP, 3)
+__global__ void __launch_bounds__(RW * Split<M>::TP, fx_inverse_min_ctas<M, MODE>())
 k_fx_inverse(GridDesc g, unsigned mask, const float2* __restrict__ spec, float* __restrict__ tau,
              const float* __restrict__ r32, double* __restrict__ partial) {
-    constexpr int E = Split<M>::E, TP = Split<M>::TP, KPT = E / TP, RS = row_stride<M>();
+    constexpr int E = Split<M>::E, TP = Split<M>::TP, RS = row_stride<M>();
     const int slot = blockIdx.y;
     if (!slot_active(g, mask, slot)) return;
     extern __shared__ __align__(16) float2 sh[];   // RW * RS
@@ -366,62 +508,22 @@ k_fx_inverse(GridDesc g, unsigned mask, const float2* __restrict__ spec, float* 
     const bool res = kRes && (g.dflags ? g.resid != 0 : true);
     const bool addr = kAddR && (g.dflags ? (g.dflags[slot] & SF_ADDR) != 0 : true);
     float2 old[E], radd[E];
-    if (res) {
-#pragma unroll
-        for (int j = 0; j < E; ++j) old[j] = out[t + TP * j];
-    }
-    if (addr) {
-        const float2* rr = reinterpret_cast<const float2*>(r32 + fbase);
-#pragma unroll
-        for (int j = 0; j < E; ++j) radd[j] = rr[t + TP * j];
-    }
-    const float2* src = spec + (long long)slot * 3 * g.NNM + row * M;
-    float2* rs = sh + r * RS;
-#pragma unroll
-    for (int j = 0; j < E; ++j) rs[t + TP * j] = src[t + TP * j];
-    __syncthreads();
-    // complex-to-real merge into the stage-1 layout
-    const float2* twN = g.tw32 + g.pN.tw_off;
+    if (res) s2_load<M>(old, out, t);
+    if (addr) s2_load<M>(radd, reinterpret_cast<const float2*>(r32 + fbase), t);
+    __shared__ float2 tws[2 * M];
+    stage_twiddles<M>(tws, g);
     float2 v[E];
-#pragma unroll
-    for (int n1 = 0; n1 < E; ++n1) {
-        const int k = TP * n1 + t;
-        float2 xk, xm;
-        if (k == 0) {
-            const float2 q = rs[0];
-            xk = make_float2(q.x, 0.f);
-            xm = make_float2(q.y, 0.f);
-        } else {
-            xk = rs[k];
-            xm = rs[M - k];
-        }
-        const float2 s = make_float2(xk.x + xm.x, xk.y - xm.y);
-        const float2 d = make_float2(xk.x - xm.x, xk.y + xm.y);
-        const float2 dw = cmulc(d, __ldg(&twN[k]));
-        v[n1] = make_float2(s.x - dw.y, s.y + dw.x);
-    }
-    __syncthreads();
-    const float2* twM = g.tw32 + g.pM.tw_off;
-    stage1_write<M, false>(v, t, twM, rs, 1);
-    __syncthreads();
-    stage2_read<M, false>(v, t, rs, 1);
-    __syncthreads();
-#pragma unroll
-    for (int i = 0; i < KPT; ++i)
-#pragma unroll
-        for (int k2 = 0; k2 < TP; ++k2) rs[t * KPT + i + E * k2] = v[i * TP + k2];
-    __syncthreads();
+    row_inverse<M, TP, E>(v, t, sh + r * RS, spec + (long long)slot * 3 * g.NNM + row * M, tws, tws + M);
     float acc = 0.f;
 #pragma unroll
     for (int j = 0; j < E; ++j) {
-        float2 x = rs[t + TP * j];
-        if (addr) x = make_float2(__fadd_rn(x.x, radd[j].x), __fadd_rn(x.y, radd[j].y));
+        if (addr) v[j] = make_float2(__fadd_rn(v[j].x, radd[j].x), __fadd_rn(v[j].y, radd[j].y));
         if (res) {
-            const float da = x.x - old[j].x, db = x.y - old[j].y;
+            const float da = v[j].x - old[j].x, db = v[j].y - old[j].y;
             acc += da * da + db * db;
         }
-        out[t + TP * j] = x;
     }
+    s2_store<M>(out, v, t);
     if (kRes) {   // uniform across the CTA (kernel argument and per-slot flag)
         const double s = block_sum_d((double)acc, red);
         if (threadIdx.x == 0 && res) partial[(long long)slot * gridDim.x + blockIdx.x] = s;
@@ -438,10 +540,11 @@ template <int M, int RW, bool ADDR, bool WTAU>
 __global__ void __launch_bounds__(RW * Split<M>::TP, 2)
 k_fx_round(GridDesc g, unsigned mask, float2* __restrict__ spec, float* __restrict__ tau,
            const float* __restrict__ r32) {
-    constexpr int E = Split<M>::E, TP = Split<M>::TP, KPT = E / TP, RS = row_stride<M>();
+    constexpr int E = Split<M>::E, TP = Split<M>::TP, RS = row_stride<M>();
     const int slot = blockIdx.y;
     if (!slot_active(g, mask, slot)) return;
     extern __shared__ __align__(16) float2 sh[];   // RW * RS
+    __shared__ float2 lut[16];
     const int N = g.N;
     const int t = threadIdx.x % TP, r = threadIdx.x / TP;
     // component fastest across CTAs (phase rows reused from L2, as in k_fx_forward)
@@ -452,87 +555,28 @@ k_fx_round(GridDesc g, unsigned mask, float2* __restrict__ spec, float* __restri
     const bool addr = ADDR && (g.dflags ? (g.dflags[slot] & SF_ADDR) != 0 : true);
     // loads for the update and the polarization: in flight during the inverse FFT
     float2 radd[E];
-    if (addr) {
-        const float2* rr = reinterpret_cast<const float2*>(r32 + fbase);
-#pragma unroll
-        for (int j = 0; j < E; ++j) radd[j] = rr[t + TP * j];
-    }
-    const uchar2* ph = reinterpret_cast<const uchar2*>(g.phase + (row % g.NN) * N);
+    if (addr) s2_load<M>(radd, reinterpret_cast<const float2*>(r32 + fbase), t);
     uchar2 q[E];
-#pragma unroll
-    for (int j = 0; j < E; ++j) q[j] = ph[TP * j + t];
+    s2_load_phase<M>(q, reinterpret_cast<const uchar2*>(g.phase + (row % g.NN) * N), t);
+    coef_pairs(lut, (float)g.Y[0], (float)g.Y[1], (float)g.Y[2]);   // read after the next barrier
     float2* sp = spec + (long long)slot * 3 * g.NNM + row * M;
     float2* rs = sh + r * RS;
-#pragma unroll
-    for (int j = 0; j < E; ++j) rs[t + TP * j] = sp[t + TP * j];
-    __syncthreads();
-    // complex-to-real merge into the stage-1 layout
-    const float2* twN = g.tw32 + g.pN.tw_off;
-    const float2* twM = g.tw32 + g.pM.tw_off;
+    __shared__ float2 tws[2 * M];
+    stage_twiddles<M>(tws, g);
+    const float2* twM = tws;
+    const float2* twN = tws + M;
     float2 v[E];
-#pragma unroll
-    for (int n1 = 0; n1 < E; ++n1) {
-        const int k = TP * n1 + t;
-        float2 xk, xm;
-        if (k == 0) {
-            const float2 z = rs[0];
-            xk = make_float2(z.x, 0.f);
-            xm = make_float2(z.y, 0.f);
-        } else {
-            xk = rs[k];
-            xm = rs[M - k];
-        }
-        const float2 s = make_float2(xk.x + xm.x, xk.y - xm.y);
-        const float2 d = make_float2(xk.x - xm.x, xk.y + xm.y);
-        const float2 dw = cmulc(d, __ldg(&twN[k]));
-        v[n1] = make_float2(s.x - dw.y, s.y + dw.x);
-    }
-    __syncthreads();
-    stage1_write<M, false>(v, t, twM, rs, 1);
-    __syncthreads();
-    stage2_read<M, false>(v, t, rs, 1);
-    __syncthreads();
-#pragma unroll
-    for (int i = 0; i < KPT; ++i)
-#pragma unroll
-        for (int k2 = 0; k2 < TP; ++k2) rs[t * KPT + i + E * k2] = v[i * TP + k2];
-    __syncthreads();
+    row_inverse<M, TP, E>(v, t, rs, sp, twM, twN);
     // update (step 7), optional store, polarization of the next sweep (step 2)
-    const float c0 = (float)g.Y[0], c1 = (float)g.Y[1], c2 = (float)g.Y[2];
-    float2* out = reinterpret_cast<float2*>(tau + fbase);
 #pragma unroll
-    for (int j = 0; j < E; ++j) {
-        float2 x = rs[t + TP * j];
-        if (addr) x = make_float2(__fadd_rn(x.x, radd[j].x), __fadd_rn(x.y, radd[j].y));
-        if (WTAU) out[t + TP * j] = x;
-        v[j] = make_float2(__fmul_rn(x.x, sel3f(q[j].x, c0, c1, c2)), __fmul_rn(x.y, sel3f(q[j].y, c0, c1, c2)));
-    }
-    __syncthreads();   // every thread has read its row values
-    stage1_write<M, true>(v, t, twM, rs, 1);
-    __syncthreads();
-    stage2_read<M, true>(v, t, rs, 1);
-    __syncthreads();
+    for (int j = 0; j < E; ++j)
+        if (addr) v[j] = make_float2(__fadd_rn(v[j].x, radd[j].x), __fadd_rn(v[j].y, radd[j].y));
+    if (WTAU) s2_store<M>(reinterpret_cast<float2*>(tau + fbase), v, t);
 #pragma unroll
-    for (int i = 0; i < KPT; ++i)
-#pragma unroll
-        for (int k2 = 0; k2 < TP; ++k2) rs[t * KPT + i + E * k2] = v[i * TP + k2];
-    __syncthreads();
-    // real-to-complex split, written over the row it came from
-#pragma unroll
-    for (int j = 0; j < E; ++j) {
-        const int k = t + TP * j;
-        const float2 z = rs[k];
-        float2 o2;
-        if (k == 0) {
-            o2 = make_float2(z.x + z.y, z.x - z.y);
-        } else {
-            const float2 zm = rs[M - k];
-            const float2 e = make_float2(0.5f * (z.x + zm.x), 0.5f * (z.y - zm.y));
-            const float2 o = make_float2(0.5f * (z.y + zm.y), -0.5f * (z.x - zm.x));
-            o2 = cadd(e, cmul(o, __ldg(&twN[k])));
-        }
-        sp[k] = o2;
-    }
+    for (int j = 0; j < E; ++j) v[j] = __fmul2_rn(v[j], lut[pair_index(q[j])]);
+    __syncthreads();   // every thread has read its stage-2 values from rs
+    // forward transform and real split, written over the row it came from
+    row_forward_split<M, TP, E>(v, t, rs, twM, twN, sp);
 }
 
 }  // namespace fast

@@ -109,14 +109,23 @@ __device__ __forceinline__ int xslot(int k1, int n2) {
 }
 template <int L> constexpr int xslots() { return L + Split<L>::E / (Split<L>::E / Split<L>::TP); }
 
+// Twiddle load from the read-only global path, or from a table staged in shared memory
+// (TWS): per-thread twiddle indices spread a warp's global loads over many L1 sectors,
+// while the shared-memory table serves them in one or two wavefronts.
+template <bool TWS>
+__device__ __forceinline__ float2 twld(const float2* tw, int i) {
+    if constexpr (TWS) return tw[i];
+    else return __ldg(&tw[i]);
+}
+
 // stage 1 (+ twiddle) and the write half of the exchange
-template <int L, bool FWD>
+template <int L, bool FWD, bool TWS = false>
 __device__ __forceinline__ void stage1_write(float2* v, int n2, const float2* __restrict__ twL, float2* sh, int pstride) {
     constexpr int E = Split<L>::E;
     RegDFT<E, FWD>::run(v);
 #pragma unroll
     for (int k1 = 1; k1 < E; ++k1) {
-        const float2 w = __ldg(&twL[(n2 * k1) % L]);
+        const float2 w = twld<TWS>(twL, (n2 * k1) % L);
         v[k1] = FWD ? cmul(v[k1], w) : cmulc(v[k1], w);
     }
 #pragma unroll
@@ -136,31 +145,39 @@ __device__ __forceinline__ void stage2_read(float2* v, int t, const float2* sh, 
     }
 }
 
-// Reverse of stage 2 for an inverse transform that starts from the stage-2 layout:
-// inverse length-TP DFTs, conjugate twiddles w_L^-(n2 k1), write for the exchange.
-template <int L>
+// A transform that starts from the stage-2 layout, v[i * TP + m] = x[(t KPT + i) + E m]
+// (the layout stage 2 leaves), runs the two stages in reverse order: length-TP DFTs over m
+// in registers, twiddles w_L^(+-(t KPT + i) k_a), the exchange, and length-E DFTs, giving
+// X[n2 + TP k_b] in v[k_b] of thread n2 (decimation in frequency:
+// X(k_a + TP k_b) = sum_p w_E^(p k_b) w_L^(p k_a) sum_m w_TP^(m k_a) x[p + E m]).
+// The inverse (FWD = false) undoes stage 2 then stage 1 of a forward transform.
+template <int L, bool FWD = false, bool TWS = false>
 __device__ __forceinline__ void rstage2_write(float2* v, int t, const float2* __restrict__ twL, float2* sh, int pstride) {
     constexpr int E = Split<L>::E, TP = Split<L>::TP, KPT = E / TP;
 #pragma unroll
     for (int i = 0; i < KPT; ++i) {
         const int k1 = t * KPT + i;
-        RegDFT<TP, false>::run(v + i * TP);
+        RegDFT<TP, FWD>::run(v + i * TP);
 #pragma unroll
         for (int n2 = 0; n2 < TP; ++n2) {
             float2 x = v[i * TP + n2];
-            if (n2 > 0 && k1 > 0) x = cmulc(x, __ldg(&twL[(n2 * k1) % L]));
+            if (n2 > 0 && k1 > 0) {
+                const float2 w = twld<TWS>(twL, (n2 * k1) % L);
+                x = FWD ? cmul(x, w) : cmulc(x, w);
+            }
             sh[xslot<L>(k1, n2) * pstride] = x;
         }
     }
 }
 
-// read half of the reverse exchange and the inverse length-E DFT: v[n1] = x[TP n1 + n2]
-template <int L>
+// read half of the reverse exchange and the length-E DFT: v[k_b] = X[n2 + TP k_b]
+// (inverse: v[n1] = x[TP n1 + n2])
+template <int L, bool FWD = false>
 __device__ __forceinline__ void rstage1_read(float2* v, int n2, const float2* sh, int pstride) {
     constexpr int E = Split<L>::E;
 #pragma unroll
     for (int k1 = 0; k1 < E; ++k1) v[k1] = sh[xslot<L>(k1, n2) * pstride];
-    RegDFT<E, false>::run(v);
+    RegDFT<E, FWD>::run(v);
 }
 
 __device__ __forceinline__ float sel3f(int ph, float a, float b, float c) { return ph == 0 ? a : (ph == 1 ? b : c); }

@@ -33,7 +33,7 @@ EXPORTS = ["hmg_version", "hmg_last_error", "hmg_create", "hmg_destroy", "hmg_vo
            "hmg_server_stats"]
 HMG_NOALLOC_MAX_N = 64
 KERNEL_KINDS = ["x_forward", "y_forward", "z_green", "y_inverse", "x_inverse", "eq_x", "eq_z", "other",
-                "x_round"]
+                "x_round", "fp64"]
 
 
 class hmg_sphere(C.Structure):
