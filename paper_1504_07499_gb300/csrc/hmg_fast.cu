@@ -151,8 +151,8 @@ k_fz3(GridDesc g, unsigned mask, float2* __restrict__ spec, double* __restrict__
     for (int i = 0; i < KPT; ++i)
 #pragma unroll
         for (int k2 = 0; k2 < TP; ++k2)
-            green_mode<float>(kx, ky, t * KPT + i + E * k2, N, scale, addb, twok0E, v[0][i * TP + k2],
-                              v[1][i * TP + k2], v[2][i * TP + k2]);
+            green_mode_fast(kx, ky, t * KPT + i + E * k2, N, scale, addb, twok0E, v[0][i * TP + k2],
+                            v[1][i * TP + k2], v[2][i * TP + k2]);
     __syncthreads();   // every thread has read the forward exchange
 #pragma unroll
     for (int c = 0; c < 3; ++c) rstage2_write<L>(v[c], t, twL, sh + c * NS + p, P);
@@ -168,7 +168,7 @@ k_fz3(GridDesc g, unsigned mask, float2* __restrict__ spec, double* __restrict__
 // Variant 1: three thread groups, one per component; the projection d . s is summed
 // through shared memory (more threads, fewer registers per thread).
 template <int L, int P, int MODE>
-__global__ void __launch_bounds__(3 * P * Split<L>::TP, 1)
+__global__ void __launch_bounds__(3 * P * Split<L>::TP, 2)
 k_fzs(GridDesc g, unsigned mask, float2* __restrict__ spec, double* __restrict__ partial) {
     constexpr int E = Split<L>::E, TP = Split<L>::TP, KPT = E / TP;
     constexpr int NS = xslots<L>() * P;
@@ -256,7 +256,8 @@ k_fzs(GridDesc g, unsigned mask, float2* __restrict__ spec, double* __restrict__
             const int q = ((i * TP + k2) * TP + t) * P;
             const float2 a = shc[q], b = sh1[q], e = sh2[q];
             const float dotA = a.x + b.x + e.x, dotB = a.y + b.y + e.y;
-            const float fA = nA > 0 ? 2.0f / (float)nA : 0.0f, fB = nB > 0 ? 2.0f / (float)nB : 0.0f;
+            const float fA = nA > 0 ? __fdividef(2.0f, (float)nA) : 0.0f;
+            const float fB = nB > 0 ? __fdividef(2.0f, (float)nB) : 0.0f;
             float2& x = v[i * TP + k2];
             x.x = scale * (x.x - fA * (float)dA * dotA);
             x.y = scale * (x.y - fB * (float)dB * dotB);

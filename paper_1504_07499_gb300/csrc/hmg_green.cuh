@@ -76,6 +76,31 @@ __device__ __forceinline__ void green_mode(int kx, int ky, int kz, int N, R scal
     }
 }
 
+// FP32 Green step of the register-resident z kernels: the same map as green_mode, with the
+// projector factor 2 / |m'|^2 from the fast reciprocal (__fdividef, error within 2 ulp)
+// and the updates as packed two-lane FP32 operations on (real, imaginary) pairs:
+// s_c <- scale s_c - (scale 2 d_c / |m'|^2) (m' . s).  The four self-conjugate modes of
+// the packed kx = 0 column (and the DC with its 2 k0 E) go through green_mode.
+__device__ __forceinline__ void green_mode_fast(int kx, int ky, int kz, int N, float scale, bool add_b,
+                                                const float* twok0E, float2& s0, float2& s1, float2& s2) {
+    const bool special = (kx == 0) && (ky == 0 || ky == N / 2) && (kz == 0 || kz == N / 2);
+    if (special) {
+        green_mode<float>(kx, ky, kz, N, scale, add_b, twok0E, s0, s1, s2);
+        return;
+    }
+    int d[3];
+    const int n2 = mode_dir(kx, signed_mode(ky, N), signed_mode(kz, N), N, d);   // > 0 off the special modes
+    const float gs = scale * __fdividef(2.0f, (float)n2);
+    const float d0 = (float)d[0], d1 = (float)d[1], d2 = (float)d[2];
+    const float2 dot = __ffma2_rn(make_float2(d2, d2), s2,
+                                  __ffma2_rn(make_float2(d1, d1), s1, __fmul2_rn(make_float2(d0, d0), s0)));
+    const float2 sc = make_float2(scale, scale);
+    const float q0 = -gs * d0, q1 = -gs * d1, q2 = -gs * d2;
+    s0 = __ffma2_rn(make_float2(q0, q0), dot, __fmul2_rn(sc, s0));
+    s1 = __ffma2_rn(make_float2(q1, q1), dot, __fmul2_rn(sc, s1));
+    s2 = __ffma2_rn(make_float2(q2, q2), dot, __fmul2_rn(sc, s2));
+}
+
 // Weighted |m' . s|^2 of packed mode (kx, ky, kz) for the equilibrium norm (integer
 // m'; the caller scales by (2 pi / N)^2 / N^6).  Modes 0 < kx < N/2 stand for kx and
 // N - kx (weight 2); the kx = 0 column holds the kx = 0 and kx = N/2 planes, whose
