@@ -275,34 +275,6 @@ k_fzs(GridDesc g, unsigned mask, float2* __restrict__ spec, double* __restrict__
 // x passes: R rows per CTA, threads (t, r) with t fastest along the row
 // ---------------------------------------------------------------------------
 
-// Real-to-complex split of one row whose M-point transform Z is in natural order in rs:
-// X[k] = e + o w_N^k with e = (Z[k] + conj Z[M-k]) / 2 and o = -i (Z[k] - conj Z[M-k]) / 2,
-// and X[M-k] = conj(e - o w_N^k) (w_N^(M-k) = -conj w_N^k); X[0] packs X(0) and X(N/2),
-// X[M/2] = conj Z[M/2].  Thread t of the row writes the pairs k = t + TP j, j < E/2.
-// twN: w_N^k, k < M, staged in shared memory.
-template <int M, int TP, int E>
-__device__ __forceinline__ void r2c_split_store(const float2* rs, const float2* __restrict__ twN,
-                                                float2* __restrict__ dst, int t) {
-#pragma unroll
-    for (int j = 0; j < E / 2; ++j) {
-        const int k = t + TP * j;
-        const float2 z = rs[k];
-        if (k == 0) {
-            dst[0] = make_float2(z.x + z.y, z.x - z.y);
-            const float2 h = rs[M / 2];
-            dst[M / 2] = make_float2(h.x, -h.y);
-        } else {
-            const float2 zm = rs[M - k];
-            const float2 e = make_float2(0.5f * (z.x + zm.x), 0.5f * (z.y - zm.y));
-            const float2 o = make_float2(0.5f * (z.y + zm.y), -0.5f * (z.x - zm.x));
-            const float2 p = cmul(o, twN[k]);
-            dst[k] = cadd(e, p);
-            const float2 q = csub(e, p);
-            dst[M - k] = make_float2(q.x, -q.y);
-        }
-    }
-}
-
 // Coefficient pairs for two neighbouring voxels of phases (a, b): lut[a | b << 2] = (c_a, c_b).
 __device__ __forceinline__ void coef_pairs(float2* lut, float c0, float c1, float c2) {
     if (threadIdx.x < 16) {
@@ -315,7 +287,7 @@ __device__ __forceinline__ void coef_pairs(float2* lut, float c0, float c1, floa
 __device__ __forceinline__ int pair_index(uchar2 q) { return q.x | (q.y << 2); }
 
 // Stage the x pass twiddles in shared memory: tws[k] = w_M^k, tws[M + k] = w_N^k (k < M).
-// Read after the caller's next barrier.
+// The caller synchronizes the CTA before the first read.
 template <int M>
 __device__ __forceinline__ void stage_twiddles(float2* tws, const GridDesc& g) {
     const float2* twM = g.tw32 + g.pM.tw_off;
@@ -386,20 +358,52 @@ __device__ __forceinline__ void s2_load_phase(uchar2* q, const uchar2* __restric
     }
 }
 
+// Lane of the same row holding the partner position M - k: a row's TP threads are TP
+// consecutive lanes; thread t's values at k = t + TP j pair with thread (TP - t) mod TP.
+template <int TP>
+__device__ __forceinline__ int partner_lane(int t) {
+    return (int)(threadIdx.x & 31u & ~(unsigned)(TP - 1)) | ((TP - t) & (TP - 1));
+}
+__device__ __forceinline__ float2 shfl2(float2 a, int lane) {
+    return make_float2(__shfl_sync(0xffffffffu, a.x, lane), __shfl_sync(0xffffffffu, a.y, lane));
+}
+
+// Real split of a row transform held as v[kb] = Z[t + TP kb] (natural positions spread over
+// the row's lanes), written to dst: X[k] = e + o w_N^k with e = (Z[k] + conj Z[M-k]) / 2,
+// o = -i (Z[k] - conj Z[M-k]) / 2; X[0] packs X(0) and X(N/2).  Z[M - k] comes from the
+// partner lane (v[E - 1 - kb]) or, for t = 0, from the thread itself (v[E - kb]).
+// twN: w_N^k, k < M, staged in shared memory.
+template <int M, int TP, int E>
+__device__ __forceinline__ void r2c_split_shfl(const float2* v, int t, const float2* twN, float2* __restrict__ dst) {
+    const int pl = partner_lane<TP>(t);
+#pragma unroll
+    for (int kb = 0; kb < E; ++kb) {
+        const int k = t + TP * kb;
+        const float2 z = v[kb];
+        float2 zm = shfl2(v[E - 1 - kb], pl);
+        if (kb > 0 && t == 0) zm = v[E - kb];
+        float2 out;
+        if (k == 0) {
+            out = make_float2(z.x + z.y, z.x - z.y);
+        } else {
+            const float2 e = make_float2(0.5f * (z.x + zm.x), 0.5f * (z.y - zm.y));
+            const float2 o = make_float2(0.5f * (z.y + zm.y), -0.5f * (z.x - zm.x));
+            out = cadd(e, cmul(o, twN[k]));
+        }
+        dst[k] = out;
+    }
+}
+
 // Forward x transform of a row held in the stage-2 layout, ending with the real split
-// written to dst: decimation-in-frequency stages, the natural-order exchange, the split.
-// Leaves the CTA synchronized on shared memory before the split.
+// written to dst: decimation-in-frequency stages (one shared-memory exchange), the split
+// with the partner values exchanged by warp shuffles.  Ends without a barrier.
 template <int M, int TP, int E>
 __device__ __forceinline__ void row_forward_split(float2* v, int t, float2* rs, const float2* __restrict__ twM,
                                                   const float2* __restrict__ twN, float2* __restrict__ dst) {
     rstage2_write<M, true, true>(v, t, twM, rs, 1);
     __syncthreads();
     rstage1_read<M, true>(v, t, rs, 1);   // v[kb] = Z[t + TP kb]
-    __syncthreads();
-#pragma unroll
-    for (int kb = 0; kb < E; ++kb) rs[t + TP * kb] = v[kb];
-    __syncthreads();
-    r2c_split_store<M, TP, E>(rs, twN, dst, t);
+    r2c_split_shfl<M, TP, E>(v, t, twN, dst);
 }
 
 template <int M, int RW, int MODE>
@@ -447,47 +451,48 @@ k_fx_forward(GridDesc g, unsigned mask, const float* __restrict__ tau, float2* _
     row_forward_split<M, TP, E>(v, t, sh + r * RS, tws, tws + M, spec + (long long)slot * 3 * g.NNM + row * M);
 }
 
-// Complex-to-real merge of a row spectrum (natural order in rs) into the stage-1 layout
-// v[n1] = x-transform input at k = TP n1 + t.  twN: w_N^k, k < M, in shared memory.
+// Complex-to-real merge with the row spectrum loaded straight into the stage-1 layout
+// (xk[n1] = X[TP n1 + t]); X[M - k] comes from the partner lane (xk[E - 1 - n1]) or, for
+// t = 0, from the thread itself (xk[E - n1]): v[n1] = (X[k] + conj X[M-k]) + i w_N^-k
+// (X[k] - conj X[M-k]), the x-transform input at k.  twN: w_N^k in shared memory.
 template <int M, int TP, int E>
-__device__ __forceinline__ void c2r_merge(float2* v, const float2* rs, const float2* __restrict__ twN, int t) {
+__device__ __forceinline__ void c2r_merge_shfl(float2* v, const float2* xk, const float2* twN, int t) {
+    const int pl = partner_lane<TP>(t);
 #pragma unroll
     for (int n1 = 0; n1 < E; ++n1) {
         const int k = TP * n1 + t;
-        float2 xk, xm;
-        if (k == 0) {
-            const float2 q = rs[0];
-            xk = make_float2(q.x, 0.f);
-            xm = make_float2(q.y, 0.f);
-        } else {
-            xk = rs[k];
-            xm = rs[M - k];
+        float2 a = xk[n1];
+        float2 b = shfl2(xk[E - 1 - n1], pl);
+        if (n1 > 0 && t == 0) b = xk[E - n1];
+        if (k == 0) {   // packed X(0) + i X(N/2)
+            b = make_float2(a.y, 0.f);
+            a = make_float2(a.x, 0.f);
         }
-        const float2 s = make_float2(xk.x + xm.x, xk.y - xm.y);
-        const float2 d = make_float2(xk.x - xm.x, xk.y + xm.y);
+        const float2 s = make_float2(a.x + b.x, a.y - b.y);
+        const float2 d = make_float2(a.x - b.x, a.y + b.y);
         const float2 dw = cmulc(d, twN[k]);
         v[n1] = make_float2(s.x - dw.y, s.y + dw.x);
     }
 }
 
-// Inverse x transform of a row spectrum: load, merge, stage 1, exchange, stage 2; leaves
-// v in the stage-2 layout (v[i TP + m] = x[(t KPT + i) + E m]).
+// Inverse x transform of a row spectrum: load into registers, merge (warp shuffles),
+// stage 1, exchange, stage 2; leaves v in the stage-2 layout (v[i TP + m] =
+// x[(t KPT + i) + E m]).  The caller has synchronized the CTA after staging twN / twM.
 template <int M, int TP, int E>
 __device__ __forceinline__ void row_inverse(float2* v, int t, float2* rs, const float2* __restrict__ src,
                                             const float2* __restrict__ twM, const float2* __restrict__ twN) {
+    float2 xk[E];
 #pragma unroll
-    for (int j = 0; j < E; ++j) rs[t + TP * j] = src[t + TP * j];
-    __syncthreads();
-    c2r_merge<M, TP, E>(v, rs, twN, t);
-    __syncthreads();
+    for (int n1 = 0; n1 < E; ++n1) xk[n1] = src[TP * n1 + t];
+    c2r_merge_shfl<M, TP, E>(v, xk, twN, t);
     stage1_write<M, false, true>(v, t, twM, rs, 1);
     __syncthreads();
     stage2_read<M, false>(v, t, rs, 1);
 }
 
-// residual sweeps that also add r hold three row fields in registers: two CTAs per SM
+// residual sweeps hold the old row (and r) in registers beside the transform: two CTAs per SM
 template <int M, int MODE>
-constexpr int fx_inverse_min_ctas() { return (MODE == XI_ADD_R_RES || Split<M>::E > 16) ? 2 : 3; }
+constexpr int fx_inverse_min_ctas() { return (MODE == XI_ADD_R_RES || MODE == XI_INPLACE_RES || Split<M>::E > 16) ? 2 : 3; }
 
 template <int M, int RW, int MODE>
 __global__ void __launch_bounds__(RW * Split<M>::TP, fx_inverse_min_ctas<M, MODE>())
@@ -513,6 +518,7 @@ k_fx_inverse(GridDesc g, unsigned mask, const float2* __restrict__ spec, float* 
     if (addr) s2_load<M>(radd, reinterpret_cast<const float2*>(r32 + fbase), t);
     __shared__ float2 tws[2 * M];
     stage_twiddles<M>(tws, g);
+    __syncthreads();
     float2 v[E];
     row_inverse<M, TP, E>(v, t, sh + r * RS, spec + (long long)slot * 3 * g.NNM + row * M, tws, tws + M);
     float acc = 0.f;
@@ -559,11 +565,12 @@ k_fx_round(GridDesc g, unsigned mask, float2* __restrict__ spec, float* __restri
     if (addr) s2_load<M>(radd, reinterpret_cast<const float2*>(r32 + fbase), t);
     uchar2 q[E];
     s2_load_phase<M>(q, reinterpret_cast<const uchar2*>(g.phase + (row % g.NN) * N), t);
-    coef_pairs(lut, (float)g.Y[0], (float)g.Y[1], (float)g.Y[2]);   // read after the next barrier
+    coef_pairs(lut, (float)g.Y[0], (float)g.Y[1], (float)g.Y[2]);
     float2* sp = spec + (long long)slot * 3 * g.NNM + row * M;
     float2* rs = sh + r * RS;
     __shared__ float2 tws[2 * M];
     stage_twiddles<M>(tws, g);
+    __syncthreads();   // tables and coefficient pairs
     const float2* twM = tws;
     const float2* twN = tws + M;
     float2 v[E];
