@@ -1,4 +1,5 @@
-"""CPU oracle for the Eyre-Milton FFT homogenization scheme -- TEST INFRASTRUCTURE ONLY.
+"""CPU oracle for the Eyre-Milton FFT homogenization scheme (and the basic scheme it is
+compared with) -- TEST INFRASTRUCTURE ONLY.
 
 Only the test suite, the smoke check and the CPU-baseline leg of the benchmark may
 import this module.  The product path (the CUDA library and its Python binding)
@@ -15,6 +16,8 @@ Everything here is plain FP64 numpy written from the paper:
 * §3, Green operator under eq. 3: Gamma0_ij(xi) = xi_i xi_j / (xi . L0 xi).
 * §3, Algorithm, steps 1-7, in the paper's order and notation (gradient form e = grad theta).
 * §3 last paragraph: <phi> = -L_hom grad Theta gives the effective tensor.
+* §3 (the list of FFT-based schemes) and eqs. 1-3: the basic scheme, the plain
+  fixed-point iteration of the Lippmann-Schwinger equation (``basic_solve``).
 
 The 3D DFT is either a direct sum (``dft3_direct``, small grids) or the library
 FFT (scipy.fft), which the tests pin against the direct sum.
@@ -23,7 +26,9 @@ Readings where the paper is silent or garbled (each is also listed in the design
 notes):
 
 * Sign of L0: taken as -k0 I with k0 > 0 in every formula, which is the only
-  reading under which the printed steps converge.
+  reading under which the printed steps converge.  The basic scheme takes the
+  positive reference +k0 I, k0 = (min k + max k) / 2, the only sign under which
+  the plain iteration converges.
 * DC of step 4 with an unnormalized DFT: the mean gradient times N^3.
 * Wavevector and Nyquist rule: m_j in (-N/2, N/2], xi_j = 2 pi m_j / N (voxel
   units).  Nyquist components (m_j = N/2, N even) are dropped from xi, except in a
@@ -299,6 +304,76 @@ def effective_tensor(phase: np.ndarray, k_phases, tol: float = 1e-8, max_iter: i
         E = np.zeros(3)
         E[j] = 1.0
         r = em_solve(phase, k_phases, E, tol, max_iter)
+        K[:, j] = -r.flux_mean
+        res.append(r)
+    return K, res
+
+
+# ---------------------------------------------------------------------------
+# §3 basic scheme (named in §3 among the FFT-based schemes; the paper prints only
+# the accelerated one).  It iterates the Lippmann-Schwinger equation of eqs. 1-3
+# directly: grad theta = grad Theta - Gamma0 * tau, tau = (L - L0) grad theta.
+# Reading: the reference medium is positive, L0 = k0 I with k0 = (min k + max k) / 2
+# (with the negative L0 of the accelerated scheme the plain iteration diverges);
+# the two convergence tests are steps 1 and 6 of the §3 Algorithm, and the new
+# iterate is the compatible field of step 5.
+# ---------------------------------------------------------------------------
+
+
+def basic_reference_k0(k_phases) -> float:
+    """k0 of the basic scheme: the centre of the conductivity range (L0 = +k0 I)."""
+    k = np.asarray(k_phases, dtype=np.float64)
+    return 0.5 * (float(k.min()) + float(k.max()))
+
+
+def basic_solve(phase: np.ndarray, k_phases, grad_Theta, tol: float = 1e-8,
+                max_iter: int = 200000, record: bool = False) -> EMResult:
+    """Basic scheme for one macroscopic gradient, in the steps of the §3 Algorithm
+    without its acceleration (step 7 keeps the compatible field)."""
+    N = phase.shape[0]
+    k_field = np.asarray(k_phases, dtype=np.float64)[phase]
+    L0 = basic_reference_k0(k_phases)             # L0 = +k0 I
+    xi = wavevectors(N)
+    E = np.asarray(grad_Theta, dtype=np.float64)
+    normE = float(np.linalg.norm(E))
+    e = np.broadcast_to(E[:, None, None, None], (3, N, N, N)).copy()
+    eps_comp = math.inf
+    hist_c, hist_q = [], []
+    eps_eq = math.inf
+    for n in range(max_iter):
+        # Step 1: convergence test on the current iterate.
+        if eps_comp < tol:
+            eps_eq, mean_phi = equilibrium_residual(k_field, e, xi)
+            hist_q.append(eps_eq)
+            if eps_eq < tol:
+                return EMResult(e, mean_phi, n, True, eps_eq, hist_c, hist_q)
+        # Polarization tau = (L - L0) grad theta (eq. 1).
+        tau = (k_field - L0)[None] * e
+        tau_hat = fft3(tau)
+        # grad theta_hat = -Gamma0 tau_hat for xi != 0, grad Theta at xi = 0 (eqs. 2-3).
+        ec_hat = -gamma0_apply(xi, L0, tau_hat)
+        ec_hat[:, 0, 0, 0] = E * N ** 3
+        ec = (ifft3_unnorm(ec_hat) / N ** 3).real
+        # Step 6: eps_comp = sqrt(<|e - e_comp|^2>) / |grad Theta|.
+        eps_comp = math.sqrt(float(((e - ec) ** 2).sum(0).mean())) / normE
+        if record:
+            hist_c.append(eps_comp)
+        if not math.isfinite(eps_comp):
+            break
+        e = ec
+    eps_eq, mean_phi = equilibrium_residual(k_field, e, xi)
+    return EMResult(e, mean_phi, max_iter, False, eps_eq, hist_c, hist_q)
+
+
+def basic_effective_tensor(phase: np.ndarray, k_phases, tol: float = 1e-8, max_iter: int = 200000):
+    """L_hom of the basic scheme for the three unit gradients (same reading of K as
+    ``effective_tensor``).  Returns (K, [EMResult] * 3)."""
+    K = np.zeros((3, 3))
+    res = []
+    for j in range(3):
+        E = np.zeros(3)
+        E[j] = 1.0
+        r = basic_solve(phase, k_phases, E, tol, max_iter)
         K[:, j] = -r.flux_mean
         res.append(r)
     return K, res
