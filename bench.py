@@ -166,10 +166,11 @@ def main() -> None:
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison solve")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
-    ap.add_argument("--mode", default="single", choices=["single", "batch", "serve", "contrast"],
+    ap.add_argument("--mode", default="single", choices=["single", "batch", "serve", "contrast", "schemes"],
                     help="single: the 256^3 RVE (default); batch: 64 mixed-size RVEs in one engine; "
                          "serve: Poisson request stream through hmg_submit/hmg_poll; "
-                         "contrast: the 256^3 RVE over 4 contrasts x 3 layers, FP32 bulk and FP64")
+                         "contrast: the 256^3 RVE over 4 contrasts x 3 layers, FP32 bulk and FP64; "
+                         "schemes: Eyre-Milton vs the basic scheme at 3 contrasts")
     ap.add_argument("--requests", type=int, default=48, help="serve mode: requests per arrival rate")
     ap.add_argument("--variant", type=int, default=-1,
                     help="pin the FP32 kernel variant of the 256^3 grid (0..7, see hmg_set_variant); "
@@ -185,6 +186,9 @@ def main() -> None:
         return
     if args.mode == "contrast":
         run_contrast(args)
+        return
+    if args.mode == "schemes":
+        run_schemes(args)
         return
     if args.mode == "serve":
         run_serve(args)
@@ -512,6 +516,57 @@ def run_contrast(args) -> None:
             "config": {"workload": "rsa256 contrast sweep: 256^3, 100 spheres at 40 % (seed 3000), l in {0.1,0.3,0.5}, "
                                    "k 0.20/0.25/{2,40,400,4000}", "precision": "fp32bulk"},
             "fp64_plain": {"voxel_iter_per_s": vox64 / t64, "seconds": t64, "speedup_fp32bulk": t64 / t32},
+            "cases": cases}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+
+
+def run_schemes(args) -> None:
+    """Accelerated (Eyre-Milton) vs basic scheme on the 256^3 RVE (100 spheres at 40 %,
+    l = 0.3, seed 3000) at contrast 10, 200 and 2000 (k_coat 2, 40, 400), both in FP32
+    bulk to tol 1e-8: sweeps per gradient against each scheme's contraction bound,
+    solve time, throughput, and the K difference between the two."""
+    import torch
+    from paper_1504_07499_gb300 import build, hmg
+    from paper_1504_07499_gb300 import inputs as I
+    build.build()
+    ctx = hmg.Context(0)
+    sl = I.generate_spheres(SEED, N_SPHERES, F_SP)
+    N = N_GRID
+    ph = torch.empty(N ** 3, dtype=torch.uint8, device="cuda")
+    hmg.hmg_voxelize(ctx.handle, torch.from_numpy(np.ascontiguousarray(sl.spheres)).cuda(), LAYER, N, ph)
+    hmg.hmg_solve(ctx.handle, ph, N, K_PHASES, TOL, hmg.HMG_FP32_BULK)     # autotune + warm-up
+    cases, vox, tt = [], 0.0, 0.0
+    for kc in (2.0, 40.0, 400.0):
+        k = (K_PHASES[0], K_PHASES[1], kc)
+        c = max(k) / min(k)
+        row = {"k_coat": kc, "contrast": c}
+        for name, sch, rho in (("eyre_milton", hmg.HMG_SCHEME_EYRE_MILTON, (np.sqrt(c) - 1) / (np.sqrt(c) + 1)),
+                               ("basic", hmg.HMG_SCHEME_BASIC, (c - 1) / (c + 1))):
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            K, info, st = hmg.hmg_solve_scheme(ctx.handle, ph, N, k, TOL, hmg.HMG_FP32_BULK, sch, max_iter=200000,
+                                               allow=(hmg.HMG_OK, hmg.HMG_NOT_CONVERGED))
+            dt = time.perf_counter() - t
+            sweeps = int(sum(info["iters"]))
+            row[name] = {"status": int(st), "sweeps_per_gradient": list(info["iters"]),
+                         "bound_sweeps": float(np.log(TOL) / np.log(rho)), "solve_s": dt,
+                         "voxel_iter_per_s": N ** 3 * sweeps / dt, "fp64_rounds": int(info.get("fp64_rounds", 0)),
+                         "K": K.tolist()}
+            vox += N ** 3 * sweeps
+            tt += dt
+        Ke, Kb = np.array(row["eyre_milton"]["K"]), np.array(row["basic"]["K"])
+        row["K_rel_diff"] = float(np.abs(Ke - Kb).max() / np.abs(Ke).max())
+        row["time_ratio_basic_over_em"] = row["basic"]["solve_s"] / row["eyre_milton"]["solve_s"]
+        cases.append(row)
+        print(json.dumps({"case": row}), file=sys.stderr, flush=True)
+    line = {"metric": "voxel-iterations/s at 256^3, Eyre-Milton and basic scheme, contrast 10..2000 "
+                      "(3 unit gradients, tol 1e-8)",
+            "value": vox / tt, "unit": UNIT, "n_gpus": 1, "steps": 2 * len(cases), "warmup": 1,
+            "ms_per_step": 1e3 * tt / (2 * len(cases)), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "rsa256 scheme comparison: 256^3, 100 spheres at 40 % (seed 3000), l = 0.3, "
+                                   "k 0.20/0.25/{2,40,400}", "precision": "fp32bulk"},
             "cases": cases}
     print(json.dumps(line), flush=True)
     ctx.close()

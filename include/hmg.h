@@ -66,6 +66,21 @@ typedef enum {
  *   same tolerance as HMG_FP64 is met (eps_eq < tol computed in FP64). */
 typedef enum { HMG_FP64 = 0, HMG_FP32_BULK = 1 } hmg_precision;
 
+/* Iterative scheme for the periodic cell problem (§3 lists the FFT-based schemes and
+ * picks the accelerated one).
+ *   HMG_SCHEME_EYRE_MILTON: the accelerated scheme of the §3 Algorithm (steps 1-7),
+ *     reference k0 = sqrt(min k * max k) (§5); contraction (sqrt c - 1)/(sqrt c + 1)
+ *     per sweep for contrast c = max k / min k.
+ *   HMG_SCHEME_BASIC: the basic scheme, the plain fixed-point iteration of the
+ *     Lippmann-Schwinger equation of §3 (eqs. 1-3), e^{n+1} = E - Gamma0 * ((k - k0) e^n)
+ *     with a positive reference k0 = (min k + max k) / 2 and Gamma0 = P / k0
+ *     (P = xi xi^T / |xi|^2); contraction (c - 1)/(c + 1) per sweep.  Steps 1 and 6
+ *     (the two convergence tests) are those of the §3 Algorithm; its new iterate is the
+ *     compatible field of step 5.
+ * Both converge to the same discrete solution (the fixed point of either is the
+ * compatible field with divergence-free flux), so K agrees to the tolerance. */
+typedef enum { HMG_SCHEME_EYRE_MILTON = 0, HMG_SCHEME_BASIC = 1 } hmg_scheme;
+
 /* Per-solve report.  Index j is the macroscopic gradient e_j. */
 typedef struct {
     int iters[3];          /* sweeps of steps 2-7 (FP32 and FP64 together) */
@@ -126,6 +141,15 @@ hmg_status hmg_solve_fields(hmg_ctx* ctx, const uint8_t* phase, int N, double k_
                             double k_incl, double k_coat, double tol,
                             hmg_precision precision, int max_iter, double K_out[9],
                             hmg_info* info, double* e_out);
+
+/* hmg_solve_fields with a choice of iterative scheme (hmg_scheme, above).  The plain
+ * FP64 form and the FP32-bulk form (FP32 sweeps with FP64 defect correction) are
+ * available for both schemes; HMG_SCHEME_EYRE_MILTON is exactly hmg_solve_fields.
+ * Errors: HMG_INVALID_ARG for an unknown scheme, otherwise as hmg_solve. */
+hmg_status hmg_solve_scheme(hmg_ctx* ctx, const uint8_t* phase, int N, double k_matrix,
+                            double k_incl, double k_coat, double tol,
+                            hmg_precision precision, hmg_scheme scheme, int max_iter,
+                            double K_out[9], hmg_info* info, double* e_out);
 
 /* Run `n_iter` sweeps of steps 2-7 of §3 (no convergence test) on a given gradient
  * field, for one macroscopic gradient grad_Theta (3 doubles, host).

@@ -118,7 +118,7 @@ std::shared_ptr<hmg::GridPlan> hmg_ctx::plan(int N) {
 namespace hmg {
 
 GridDesc make_desc(const GridPlan& gp, bool fp64, const double k[3], const uint8_t* phase_d,
-                   int nslots) {
+                   int nslots, int scheme) {
     GridDesc g;
     memset(&g, 0, sizeof(g));
     const int N = gp.N, M = N / 2;
@@ -133,12 +133,34 @@ GridDesc make_desc(const GridPlan& gp, bool fp64, const double k[3], const uint8
     g.tw64 = gp.tw64;
     const double kmin = std::min(k[0], std::min(k[1], k[2]));
     const double kmax = std::max(k[0], std::max(k[1], k[2]));
-    const double k0 = std::sqrt(kmin * kmax);
-    g.k0 = k0;
-    for (int p = 0; p < 3; ++p) {
-        g.Y[p] = (k[p] - k0) / (k[p] + k0);
-        g.W[p] = k[p] / (k[p] + k0);
-        g.KP[p] = k[p] + k0;
+    g.scheme = scheme;
+    if (scheme == HMG_SCHEME_BASIC) {
+        // basic scheme: positive reference medium at the centre of the conductivity range,
+        // e^{n+1} = E - Gamma0 * ((k - k0) e^n) with Gamma0 = P / k0, on the field e itself
+        const double k0 = 0.5 * (kmin + kmax);
+        g.k0 = k0;
+        for (int p = 0; p < 3; ++p) {
+            g.Y[p] = (k[p] - k0) / k0;
+            g.W[p] = k[p];
+            g.KP[p] = 1.0;
+        }
+        g.ga = 0.0;
+        g.gb = 1.0;
+        g.gc = 1.0;
+        g.epsf = 1.0;
+    } else {
+        // Eyre-Milton (tau = (k + k0) e): tau^{n+1} = (I - 2P)(Y tau^n) + 2 k0 E
+        const double k0 = std::sqrt(kmin * kmax);
+        g.k0 = k0;
+        for (int p = 0; p < 3; ++p) {
+            g.Y[p] = (k[p] - k0) / (k[p] + k0);
+            g.W[p] = k[p] / (k[p] + k0);
+            g.KP[p] = k[p] + k0;
+        }
+        g.ga = 1.0;
+        g.gb = 2.0;
+        g.gc = 2.0 * k0;
+        g.epsf = 1.0 / (2.0 * k0);
     }
     for (int s = 0; s < kMaxSlots; ++s)
         for (int c = 0; c < 3; ++c) g.E[s][c] = (s == c) ? 1.0 : 0.0;
@@ -484,11 +506,13 @@ bool Solver::fetch(double* h, int off, int count) {
     return true;
 }
 
-// eps_comp from the sum of squared tau differences: |e^n - e_comp^n| = |dtau| / (2 k0)
+// eps_comp from the sum of squared differences of the stored field between two sweeps:
+// |e^n - e_comp^n| = |dtau| / (2 k0) for Eyre-Milton, = |de| for the basic scheme
+// (its new iterate is e_comp^n)
 double Solver::eps_from_sum(double sum, int slot) const {
     const double nE = std::sqrt(g.E[slot][0] * g.E[slot][0] + g.E[slot][1] * g.E[slot][1] +
                                 g.E[slot][2] * g.E[slot][2]);
-    return std::sqrt(sum / (double)g.N3) / (2.0 * g.k0 * nE);
+    return std::sqrt(sum / (double)g.N3) * g.epsf / nE;
 }
 
 // eq check of the slots in `mask`; fills eps_eq and the mean flux <k e>
@@ -577,6 +601,13 @@ hmg_status Solver::run_bulk(int max_iter, double tol, hmg_info* info, double K[9
     const double thetaA = std::max(tol, 1e-6);
     const double eta = 1e-4;           // inner solves reduce the outer residual by this factor
     const int stall = 24;              // sweeps without a new best residual = FP32 floor
+    // a new best must improve by this factor; the basic scheme contracts by only
+    // rho = max|Y| = (c - 1) / (c + 1) per sweep, so its bar follows rho
+    double rho = 0.0;
+    for (int p = 0; p < 3; ++p) rho = std::max(rho, std::fabs(g.Y[p]));
+    const double improve = g.scheme == HMG_SCHEME_BASIC
+                               ? std::min(0.999, 1.0 - 0.25 * (1.0 - std::pow(rho, (double)kResidualEvery)))
+                               : 0.999;
     auto mask_of = [&](int ph) {
         unsigned m = 0;
         for (int sl = 0; sl < g.nslots; ++sl)
@@ -672,7 +703,7 @@ hmg_status Solver::run_bulk(int max_iter, double tol, hmg_info* info, double K[9
                 state[sl] = PH_DONE;
                 continue;
             }
-            if (eps32[sl] < best[sl] * 0.999) {
+            if (eps32[sl] < best[sl] * improve) {
                 best[sl] = eps32[sl];
                 since_best[sl] = 0;
             } else {

@@ -145,13 +145,13 @@ k_fz3(GridDesc g, unsigned mask, float2* __restrict__ spec, double* __restrict__
     // Green operator on the registers, then the inverse back to natural order
     const bool addb = g.dflags ? (g.dflags[slot] & SF_ADDB) != 0 : MODE == Z_ITER;
     const float scale = (float)(1.0 / (double)g.N3);
-    const float twok0E[3] = {(float)(2.0 * g.k0 * g.E[slot][0]), (float)(2.0 * g.k0 * g.E[slot][1]),
-                             (float)(2.0 * g.k0 * g.E[slot][2])};
+    const float cE[3] = {(float)(g.gc * g.E[slot][0]), (float)(g.gc * g.E[slot][1]), (float)(g.gc * g.E[slot][2])};
+    const float ga = (float)g.ga, gb = (float)g.gb;
 #pragma unroll
     for (int i = 0; i < KPT; ++i)
 #pragma unroll
         for (int k2 = 0; k2 < TP; ++k2)
-            green_mode_fast(kx, ky, t * KPT + i + E * k2, N, scale, addb, twok0E, v[0][i * TP + k2],
+            green_mode_fast(kx, ky, t * KPT + i + E * k2, N, scale, ga, gb, addb, cE, v[0][i * TP + k2],
                             v[1][i * TP + k2], v[2][i * TP + k2]);
     __syncthreads();   // every thread has read the forward exchange
 #pragma unroll
@@ -245,7 +245,8 @@ k_fzs(GridDesc g, unsigned mask, float2* __restrict__ spec, double* __restrict__
     }
     const bool addb = g.dflags ? (g.dflags[slot] & SF_ADDB) != 0 : MODE == Z_ITER;
     const float scale = (float)(1.0 / (double)g.N3);
-    const float twok0E = (float)(2.0 * g.k0 * g.E[slot][c]);
+    const float cE = (float)(g.gc * g.E[slot][c]);
+    const float ga = (float)g.ga, gb = (float)g.gb;
 #pragma unroll
     for (int i = 0; i < KPT; ++i)
 #pragma unroll
@@ -256,12 +257,12 @@ k_fzs(GridDesc g, unsigned mask, float2* __restrict__ spec, double* __restrict__
             const int q = ((i * TP + k2) * TP + t) * P;
             const float2 a = shc[q], b = sh1[q], e = sh2[q];
             const float dotA = a.x + b.x + e.x, dotB = a.y + b.y + e.y;
-            const float fA = nA > 0 ? __fdividef(2.0f, (float)nA) : 0.0f;
-            const float fB = nB > 0 ? __fdividef(2.0f, (float)nB) : 0.0f;
+            const float fA = nA > 0 ? __fdividef(gb, (float)nA) : 0.0f;
+            const float fB = nB > 0 ? __fdividef(gb, (float)nB) : 0.0f;
             float2& x = v[i * TP + k2];
-            x.x = scale * (x.x - fA * (float)dA * dotA);
-            x.y = scale * (x.y - fB * (float)dB * dotB);
-            if (addb && kx == 0 && ky == 0 && kz == 0) x.x += twok0E;
+            x.x = scale * (ga * x.x - fA * (float)dA * dotA);
+            x.y = scale * (ga * x.y - fB * (float)dB * dotB);
+            if (addb && kx == 0 && ky == 0 && kz == 0) x.x += cE;
         }
     __syncthreads();   // every thread has read the shares
     rstage2_write<L>(v, t, twL, shc, P);

@@ -33,6 +33,12 @@ struct GridDesc {
     double W[3];           // k/(k + k0): flux factor, phi = W tau
     double KP[3];          // k + k0: tau = (k + k0) e
     double k0;
+    // Scheme (hmg_scheme) and its Green step s <- scale (ga s - gb P s) + gc E at the DC
+    // mode; the sweep residual |e^n - e_comp^n| is epsf |field^n - field^{n+1}|.
+    // Eyre-Milton (tau form): ga = 1, gb = 2, gc = 2 k0, epsf = 1 / (2 k0);
+    // basic scheme (field e, Y = (k - k0) / k0, W = k, KP = 1): ga = 0, gb = 1, gc = 1, epsf = 1.
+    int scheme;
+    double ga, gb, gc, epsf;
     double E[kMaxSlots][3];  // macroscopic gradient of each right-hand side
     int nslots;            // right-hand sides held in the fields
     int rows;              // x-pass rows per CTA

@@ -262,8 +262,8 @@ k_z_pass(GridDesc g, unsigned mask, typename Cplx<R>::T* __restrict__ spec, doub
     if (MODE == Z_ITER || MODE == Z_ITER_NOB || MODE == Z_EQ) {
         const bool addb = g.dflags ? (g.dflags[slot] & SF_ADDB) != 0 : MODE == Z_ITER;
         const R scale = R(1.0 / (double)g.N3);
-        const R twok0E[3] = {R(2.0 * g.k0 * g.E[slot][0]), R(2.0 * g.k0 * g.E[slot][1]),
-                             R(2.0 * g.k0 * g.E[slot][2])};
+        const R cE[3] = {R(g.gc * g.E[slot][0]), R(g.gc * g.E[slot][1]), R(g.gc * g.E[slot][2])};
+        const R ga = R(g.ga), gb = R(g.gb);
         double acc = 0.0;
         const double twopi_n = 6.283185307179586476925 / (double)N;
         for (int q = threadIdx.x; q < N * P; q += blockDim.x) {
@@ -274,7 +274,7 @@ k_z_pass(GridDesc g, unsigned mask, typename Cplx<R>::T* __restrict__ spec, doub
             if (MODE == Z_EQ) {
                 acc += eq_mode(kx, ky, kz, N, s0, s1, s2);
             } else {
-                green_mode<R>(kx, ky, kz, N, scale, addb, twok0E, s0, s1, s2);
+                green_mode<R>(kx, ky, kz, N, scale, ga, gb, addb, cE, s0, s1, s2);
                 e[0] = s0;
                 e[P] = s1;
                 e[2 * P] = s2;

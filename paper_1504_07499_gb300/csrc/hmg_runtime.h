@@ -53,7 +53,8 @@ struct SolveState {
     void free_all(::hmg_ctx* c);
 };
 
-GridDesc make_desc(const GridPlan& gp, bool fp64, const double k[3], const uint8_t* phase_d, int nslots);
+GridDesc make_desc(const GridPlan& gp, bool fp64, const double k[3], const uint8_t* phase_d, int nslots,
+                   int scheme = HMG_SCHEME_EYRE_MILTON);
 
 // Pick the faster z-pass variant of the FP32 register-resident path for g.N by timing
 // both on the state's spectrum buffer (its contents are scratch); cached per context.
