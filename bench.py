@@ -39,11 +39,12 @@ UNIT = "voxel-iter/s"
 
 
 def workload_config(precision: str) -> dict:
-    return {"workload": "rsa256: 256^3 RVE, 100 spheres at 40% (RSA + growth sweeps), layer 0.3, "
+    state_gb = 1.4 * (N_GRID / 256) ** 3
+    return {"workload": f"rsa{N_GRID}: {N_GRID}^3 RVE, 100 spheres at 40% (RSA + growth sweeps), layer 0.3, "
                         "k 0.20/0.25/400 (contrast 2000), tol 1e-8, 3 unit gradients",
             "N": N_GRID, "n_spheres": N_SPHERES, "f_sp": F_SP, "layer": LAYER, "k": list(K_PHASES),
             "tol": TOL, "precision": precision, "seed": SEED,
-            "l2": "inputs larger than L2 (solver fields 1.4 GB vs 129 MB L2), no flush"}
+            "l2": f"inputs larger than L2 (solver fields {state_gb:.1f} GB vs 129 MB L2), no flush"}
 
 
 def measured_peaks() -> dict:
@@ -175,9 +176,15 @@ def main() -> None:
     ap.add_argument("--variant", type=int, default=-1,
                     help="pin the FP32 kernel variant of the 256^3 grid (0..7, see hmg_set_variant); "
                          "default: autotuned on the device")
+    ap.add_argument("--grid", type=int, default=256, choices=[256, 512],
+                    help="single mode: grid size of the RVE (256 is the benchmark workload; 512 the "
+                         "largest grid, the same spheres at twice the resolution)")
     ap.add_argument("--sweeps-only", type=int, default=0,
                     help="profiling case: voxelize, run this many sweeps of one gradient, exit")
     args = ap.parse_args()
+    global N_GRID, METRIC
+    N_GRID = args.grid
+    METRIC = METRIC.replace("256^3", f"{N_GRID}^3")
     if args.impl == "reference":
         run_reference(args)
         return

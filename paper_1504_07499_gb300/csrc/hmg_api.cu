@@ -165,16 +165,20 @@ GridDesc make_desc(const GridPlan& gp, bool fp64, const double k[3], const uint8
     for (int s = 0; s < kMaxSlots; ++s)
         for (int c = 0; c < 3; ++c) g.E[s][c] = (s == c) ? 1.0 : 0.0;
     g.nslots = nslots;
-    const int tile = fp64 ? 1024 : 2048;        // complex values per x-pass CTA buffer
-    int rows = 1;
-    while (rows * 2 * M <= tile) rows *= 2;
-    rows = std::min(rows, pow2_divisor(g.NN));
-    g.rows = rows;
-    const int pm = pow2_divisor(M);
-    g.Py = std::min(fp64 ? 8 : 16, pm);
-    g.Pz = std::min(fp64 ? 4 : 8, pm);
+    set_tiles(g, fp64);
     g.phase = phase_d;
     return g;
+}
+
+void set_tiles(GridDesc& g, bool fp64) {
+    const int tile = fp64 ? 1024 : 2048;        // complex values per x-pass CTA buffer
+    int rows = 1;
+    while (rows * 2 * g.M <= tile) rows *= 2;
+    rows = std::min(rows, pow2_divisor(g.NN));
+    g.rows = rows;
+    const int pm = pow2_divisor(g.M);
+    g.Py = std::min(fp64 ? 8 : 16, pm);
+    g.Pz = std::min(fp64 ? 4 : 8, pm);
 }
 
 static float time_launches(cudaStream_t st, const std::function<void()>& f, int reps) {

@@ -28,8 +28,13 @@ namespace fast {
 // y pass: P consecutive kx columns of one (component, z) plane; threads (p, t)
 // ---------------------------------------------------------------------------
 
+// CTAs per SM the register bound of a pass kernel aims at: long columns (32 values per
+// thread) get more registers
+template <int L, int base>
+constexpr int col_min_ctas() { return Split<L>::E > 24 ? base - 1 : base; }
+
 template <int L, int P, bool FWD>
-__global__ void __launch_bounds__(P * Split<L>::TP, 3)
+__global__ void __launch_bounds__(P * Split<L>::TP, col_min_ctas<L, 3>())
 k_fy(GridDesc g, unsigned mask, float2* __restrict__ spec) {
     constexpr int E = Split<L>::E, TP = Split<L>::TP;
     const int slot = blockIdx.y;
@@ -168,7 +173,7 @@ k_fz3(GridDesc g, unsigned mask, float2* __restrict__ spec, double* __restrict__
 // Variant 1: three thread groups, one per component; the projection d . s is summed
 // through shared memory (more threads, fewer registers per thread).
 template <int L, int P, int MODE>
-__global__ void __launch_bounds__(3 * P * Split<L>::TP, 2)
+__global__ void __launch_bounds__(3 * P * Split<L>::TP, col_min_ctas<L, 2>())
 k_fzs(GridDesc g, unsigned mask, float2* __restrict__ spec, double* __restrict__ partial) {
     constexpr int E = Split<L>::E, TP = Split<L>::TP, KPT = E / TP;
     constexpr int NS = xslots<L>() * P;
@@ -632,6 +637,7 @@ bool fast_y(const GridDesc& g, bool fwd, unsigned mask, void* spec, cudaStream_t
         HMG_FAST_LEN(128, FY)
         HMG_FAST_LEN(192, FY)
         HMG_FAST_LEN(256, FY)
+        HMG_FAST_LEN(512, FY)
         default: return false;
     }
 #undef FY
@@ -645,49 +651,68 @@ int fast_z_ctas(const GridDesc& g) {
         case 128: P = fz_cols<128>(); break;
         case 192: P = fz_cols<192>(); break;
         case 256: P = fz_cols<256>(); break;
+        case 512: P = fz_cols<512>(); break;
         default: return 0;
     }
     if (g.M % P) return 0;
     return g.N * (g.M / P);
 }
 
+namespace {
+template <int L, int P>
+void launch_fzs(int mode, dim3 grid, size_t sm, cudaStream_t st, const GridDesc& g, unsigned mask, float2* sp,
+                double* partial) {
+    constexpr int T = 3 * P * fast::Split<L>::TP;
+    switch (mode) {
+        case Z_FWD: launch_dyn(fast::k_fzs<L, P, Z_FWD>, grid, T, sm, st, g, mask, sp, partial); break;
+        case Z_INV: launch_dyn(fast::k_fzs<L, P, Z_INV>, grid, T, sm, st, g, mask, sp, partial); break;
+        case Z_ITER: launch_dyn(fast::k_fzs<L, P, Z_ITER>, grid, T, sm, st, g, mask, sp, partial); break;
+        case Z_ITER_NOB: launch_dyn(fast::k_fzs<L, P, Z_ITER_NOB>, grid, T, sm, st, g, mask, sp, partial); break;
+        default: launch_dyn(fast::k_fzs<L, P, Z_EQ>, grid, T, sm, st, g, mask, sp, partial); break;
+    }
+}
+template <int L, int P>
+void launch_fz3(int mode, dim3 grid, size_t sm, cudaStream_t st, const GridDesc& g, unsigned mask, float2* sp,
+                double* partial) {
+    constexpr int T = P * fast::Split<L>::TP;
+    switch (mode) {
+        case Z_FWD: launch_dyn(fast::k_fz3<L, P, Z_FWD>, grid, T, sm, st, g, mask, sp, partial); break;
+        case Z_INV: launch_dyn(fast::k_fz3<L, P, Z_INV>, grid, T, sm, st, g, mask, sp, partial); break;
+        case Z_ITER: launch_dyn(fast::k_fz3<L, P, Z_ITER>, grid, T, sm, st, g, mask, sp, partial); break;
+        case Z_ITER_NOB: launch_dyn(fast::k_fz3<L, P, Z_ITER_NOB>, grid, T, sm, st, g, mask, sp, partial); break;
+        default: launch_dyn(fast::k_fz3<L, P, Z_EQ>, grid, T, sm, st, g, mask, sp, partial); break;
+    }
+}
+// z pass of length L: the three-components-per-thread kernel (variant 0) holds 3 E complex
+// values per thread and exists up to E = 24 (L <= 256); longer columns always use the
+// per-component thread groups (variant 1).
+template <int L>
+bool fast_z_len(const GridDesc& g, int mode, unsigned mask, float2* sp, double* partial, cudaStream_t st) {
+    constexpr int P = fz_cols<L>();
+    if (g.M % P) return false;
+    dim3 grid(g.N * (g.M / P), g.nslots);
+    const size_t sm = sizeof(float2) * 3 * fast::xslots<L>() * P;
+    if constexpr (fast::Split<L>::E > 24) {
+        launch_fzs<L, P>(mode, grid, sm, st, g, mask, sp, partial);
+    } else {
+        if (g.zvar == 1) launch_fzs<L, P>(mode, grid, sm, st, g, mask, sp, partial);
+        else launch_fz3<L, P>(mode, grid, sm, st, g, mask, sp, partial);
+    }
+    return true;
+}
+}  // namespace
+
 bool fast_z(const GridDesc& g, int mode, unsigned mask, void* spec, double* partial, cudaStream_t st) {
     float2* sp = reinterpret_cast<float2*>(spec);
-#define FZ(L)                                                                                          \
-    {                                                                                                  \
-        constexpr int P = fz_cols<L>();                                                                \
-        if (g.M % P) return false;                                                                     \
-        dim3 grid(g.N * (g.M / P), g.nslots);                                                          \
-        const size_t sm = sizeof(float2) * 3 * fast::xslots<L>() * P;                                  \
-        if (g.zvar == 1) {                                                                             \
-            constexpr int T = 3 * P * fast::Split<L>::TP;                                              \
-            switch (mode) {                                                                            \
-                case Z_FWD: launch_dyn(fast::k_fzs<L, P, Z_FWD>, grid, T, sm, st, g, mask, sp, partial); break;   \
-                case Z_INV: launch_dyn(fast::k_fzs<L, P, Z_INV>, grid, T, sm, st, g, mask, sp, partial); break;   \
-                case Z_ITER: launch_dyn(fast::k_fzs<L, P, Z_ITER>, grid, T, sm, st, g, mask, sp, partial); break; \
-                case Z_ITER_NOB: launch_dyn(fast::k_fzs<L, P, Z_ITER_NOB>, grid, T, sm, st, g, mask, sp, partial); break; \
-                default: launch_dyn(fast::k_fzs<L, P, Z_EQ>, grid, T, sm, st, g, mask, sp, partial); break;       \
-            }                                                                                          \
-        } else {                                                                                       \
-            constexpr int T = P * fast::Split<L>::TP;                                                  \
-            switch (mode) {                                                                            \
-                case Z_FWD: launch_dyn(fast::k_fz3<L, P, Z_FWD>, grid, T, sm, st, g, mask, sp, partial); break;   \
-                case Z_INV: launch_dyn(fast::k_fz3<L, P, Z_INV>, grid, T, sm, st, g, mask, sp, partial); break;   \
-                case Z_ITER: launch_dyn(fast::k_fz3<L, P, Z_ITER>, grid, T, sm, st, g, mask, sp, partial); break; \
-                case Z_ITER_NOB: launch_dyn(fast::k_fz3<L, P, Z_ITER_NOB>, grid, T, sm, st, g, mask, sp, partial); break; \
-                default: launch_dyn(fast::k_fz3<L, P, Z_EQ>, grid, T, sm, st, g, mask, sp, partial); break;       \
-            }                                                                                          \
-        }                                                                                              \
-    }
     switch (g.N) {
-        HMG_FAST_LEN(64, FZ)
-        HMG_FAST_LEN(96, FZ)
-        HMG_FAST_LEN(128, FZ)
-        HMG_FAST_LEN(192, FZ)
-        HMG_FAST_LEN(256, FZ)
+        case 64: return fast_z_len<64>(g, mode, mask, sp, partial, st);
+        case 96: return fast_z_len<96>(g, mode, mask, sp, partial, st);
+        case 128: return fast_z_len<128>(g, mode, mask, sp, partial, st);
+        case 192: return fast_z_len<192>(g, mode, mask, sp, partial, st);
+        case 256: return fast_z_len<256>(g, mode, mask, sp, partial, st);
+        case 512: return fast_z_len<512>(g, mode, mask, sp, partial, st);
         default: return false;
     }
-#undef FZ
 }
 
 int fast_x_ctas(const GridDesc& g) {
@@ -698,6 +723,7 @@ int fast_x_ctas(const GridDesc& g) {
         case 64: RW = fx_rows<64>(); break;
         case 96: RW = fx_rows<96>(); break;
         case 128: RW = fx_rows<128>(); break;
+        case 256: RW = fx_rows<256>(); break;
         default: return 0;
     }
     if ((3 * g.NN) % RW || g.NN % RW) return 0;
@@ -724,6 +750,7 @@ bool fast_x_forward(const GridDesc& g, int mode, unsigned mask, const float* tau
         HMG_FAST_LEN(64, FXF)
         HMG_FAST_LEN(96, FXF)
         HMG_FAST_LEN(128, FXF)
+        HMG_FAST_LEN(256, FXF)
         default: return false;
     }
 #undef FXF
@@ -752,6 +779,7 @@ bool fast_x_inverse(const GridDesc& g, int mode, unsigned mask, const void* spec
         HMG_FAST_LEN(64, FXI)
         HMG_FAST_LEN(96, FXI)
         HMG_FAST_LEN(128, FXI)
+        HMG_FAST_LEN(256, FXI)
         default: return false;
     }
 #undef FXI
@@ -782,6 +810,7 @@ bool fast_x_round(const GridDesc& g, bool addr, bool wtau, unsigned mask, void* 
         HMG_FAST_LEN(64, FXR)
         HMG_FAST_LEN(96, FXR)
         HMG_FAST_LEN(128, FXR)
+        HMG_FAST_LEN(256, FXR)
         default: return false;
     }
 #undef FXR

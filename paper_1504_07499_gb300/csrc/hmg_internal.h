@@ -85,6 +85,10 @@ void launch_x_inverse(const GridDesc& g, int mode, unsigned mask, const void* sp
                       const float* r32, float* d32, float* r32_out, double* partial,
                       cudaStream_t st);
 
+// Tile sizes of the generic shared-memory passes (x rows per CTA, y and z columns per CTA)
+// for FP32 or FP64 elements.  FP64 launches always take the FP64 tiles, whatever the
+// descriptor says (the FP32-bulk solver runs its FP64 work on its FP32 descriptor).
+void set_tiles(GridDesc& g, bool fp64);
 int x_ctas(const GridDesc& g);   // CTAs per right-hand side of the generic x passes
 int z_ctas(const GridDesc& g);   // CTAs per right-hand side of the generic z pass
 // CTAs per right-hand side of the x / z passes that launch_* runs for precision R

@@ -387,12 +387,20 @@ template <> int x_ctas_for<float>(const GridDesc& g) {
     const int f = fast_x_ctas(g);
     return f ? f : x_ctas(g);
 }
-template <> int x_ctas_for<double>(const GridDesc& g) { return x_ctas(g); }
+template <> int x_ctas_for<double>(const GridDesc& g) {
+    GridDesc t = g;
+    set_tiles(t, true);
+    return x_ctas(t);
+}
 template <> int z_ctas_for<float>(const GridDesc& g) {
     const int f = fast_z_ctas(g);
     return f ? f : z_ctas(g);
 }
-template <> int z_ctas_for<double>(const GridDesc& g) { return z_ctas(g); }
+template <> int z_ctas_for<double>(const GridDesc& g) {
+    GridDesc t = g;
+    set_tiles(t, true);
+    return z_ctas(t);
+}
 
 template <typename R, typename K>
 static void set_smem(K kern, size_t bytes) {
@@ -407,18 +415,20 @@ void launch_x_forward(const GridDesc& g, int mode, unsigned mask, const R* tau, 
     if constexpr (std::is_same<R, float>::value) {
         if (fast_x_forward(g, mode, mask, tau, spec, partial, st)) return;
     }
-    const size_t sm = 2ull * g.rows * g.M * sizeof(T2);
-    dim3 grid(x_ctas(g), g.nslots);
+    GridDesc t = g;   // FP64 passes take the FP64 tiles
+    if constexpr (std::is_same<R, double>::value) set_tiles(t, true);
+    const size_t sm = 2ull * t.rows * t.M * sizeof(T2);
+    dim3 grid(x_ctas(t), t.nslots);
     T2* sp = reinterpret_cast<T2*>(spec);
     if (mode == XF_PLAIN) {
         set_smem<R>(k_x_forward<R, XF_PLAIN>, sm);
-        k_x_forward<R, XF_PLAIN><<<grid, kThreads, sm, st>>>(g, mask, tau, sp, partial);
+        k_x_forward<R, XF_PLAIN><<<grid, kThreads, sm, st>>>(t, mask, tau, sp, partial);
     } else if (mode == XF_POLARIZE) {
         set_smem<R>(k_x_forward<R, XF_POLARIZE>, sm);
-        k_x_forward<R, XF_POLARIZE><<<grid, kThreads, sm, st>>>(g, mask, tau, sp, partial);
+        k_x_forward<R, XF_POLARIZE><<<grid, kThreads, sm, st>>>(t, mask, tau, sp, partial);
     } else {
         set_smem<R>(k_x_forward<R, XF_FLUX>, sm);
-        k_x_forward<R, XF_FLUX><<<grid, kThreads, sm, st>>>(g, mask, tau, sp, partial);
+        k_x_forward<R, XF_FLUX><<<grid, kThreads, sm, st>>>(t, mask, tau, sp, partial);
     }
 }
 
@@ -428,15 +438,17 @@ void launch_y_pass(const GridDesc& g, bool forward, unsigned mask, void* spec, c
     if constexpr (std::is_same<R, float>::value) {
         if (fast_y(g, forward, mask, spec, st)) return;
     }
-    const size_t sm = 2ull * g.N * g.Py * sizeof(T2);
-    dim3 grid(3 * g.N * (g.M / g.Py), g.nslots);
+    GridDesc t = g;   // FP64 passes take the FP64 tiles
+    if constexpr (std::is_same<R, double>::value) set_tiles(t, true);
+    const size_t sm = 2ull * t.N * t.Py * sizeof(T2);
+    dim3 grid(3 * t.N * (t.M / t.Py), t.nslots);
     T2* sp = reinterpret_cast<T2*>(spec);
     if (forward) {
         set_smem<R>(k_y_pass<R, true>, sm);
-        k_y_pass<R, true><<<grid, kThreads, sm, st>>>(g, mask, sp);
+        k_y_pass<R, true><<<grid, kThreads, sm, st>>>(t, mask, sp);
     } else {
         set_smem<R>(k_y_pass<R, false>, sm);
-        k_y_pass<R, false><<<grid, kThreads, sm, st>>>(g, mask, sp);
+        k_y_pass<R, false><<<grid, kThreads, sm, st>>>(t, mask, sp);
     }
 }
 
@@ -446,29 +458,31 @@ void launch_z_pass(const GridDesc& g, int mode, unsigned mask, void* spec, doubl
     if constexpr (std::is_same<R, float>::value) {
         if (fast_z(g, mode, mask, spec, partial, st)) return;
     }
-    const size_t sm = 2ull * 3 * g.N * g.Pz * sizeof(T2);
-    dim3 grid(z_ctas(g), g.nslots);
+    GridDesc t = g;   // FP64 passes take the FP64 tiles
+    if constexpr (std::is_same<R, double>::value) set_tiles(t, true);
+    const size_t sm = 2ull * 3 * t.N * t.Pz * sizeof(T2);
+    dim3 grid(z_ctas(t), t.nslots);
     T2* sp = reinterpret_cast<T2*>(spec);
     switch (mode) {
         case Z_FWD:
             set_smem<R>(k_z_pass<R, Z_FWD>, sm);
-            k_z_pass<R, Z_FWD><<<grid, kThreads, sm, st>>>(g, mask, sp, partial);
+            k_z_pass<R, Z_FWD><<<grid, kThreads, sm, st>>>(t, mask, sp, partial);
             break;
         case Z_INV:
             set_smem<R>(k_z_pass<R, Z_INV>, sm);
-            k_z_pass<R, Z_INV><<<grid, kThreads, sm, st>>>(g, mask, sp, partial);
+            k_z_pass<R, Z_INV><<<grid, kThreads, sm, st>>>(t, mask, sp, partial);
             break;
         case Z_ITER:
             set_smem<R>(k_z_pass<R, Z_ITER>, sm);
-            k_z_pass<R, Z_ITER><<<grid, kThreads, sm, st>>>(g, mask, sp, partial);
+            k_z_pass<R, Z_ITER><<<grid, kThreads, sm, st>>>(t, mask, sp, partial);
             break;
         case Z_ITER_NOB:
             set_smem<R>(k_z_pass<R, Z_ITER_NOB>, sm);
-            k_z_pass<R, Z_ITER_NOB><<<grid, kThreads, sm, st>>>(g, mask, sp, partial);
+            k_z_pass<R, Z_ITER_NOB><<<grid, kThreads, sm, st>>>(t, mask, sp, partial);
             break;
         default:
             set_smem<R>(k_z_pass<R, Z_EQ>, sm);
-            k_z_pass<R, Z_EQ><<<grid, kThreads, sm, st>>>(g, mask, sp, partial);
+            k_z_pass<R, Z_EQ><<<grid, kThreads, sm, st>>>(t, mask, sp, partial);
             break;
     }
 }
@@ -480,12 +494,14 @@ void launch_x_inverse(const GridDesc& g, int mode, unsigned mask, const void* sp
     if constexpr (std::is_same<R, float>::value) {
         if (fast_x_inverse(g, mode, mask, spec, tau, r32, partial, st)) return;
     }
-    const size_t sm = 2ull * g.rows * g.M * sizeof(T2);
-    dim3 grid(x_ctas(g), g.nslots);
+    GridDesc t = g;   // FP64 passes take the FP64 tiles
+    if constexpr (std::is_same<R, double>::value) set_tiles(t, true);
+    const size_t sm = 2ull * t.rows * t.M * sizeof(T2);
+    dim3 grid(x_ctas(t), t.nslots);
     const T2* sp = reinterpret_cast<const T2*>(spec);
 #define HMG_XI(MODE_)                                                                        \
     set_smem<R>(k_x_inverse<R, MODE_>, sm);                                                  \
-    k_x_inverse<R, MODE_><<<grid, kThreads, sm, st>>>(g, mask, sp, tau, r32, d32, r32_out, partial)
+    k_x_inverse<R, MODE_><<<grid, kThreads, sm, st>>>(t, mask, sp, tau, r32, d32, r32_out, partial)
     switch (mode) {
         case XI_PLAIN: HMG_XI(XI_PLAIN); break;
         case XI_INPLACE: HMG_XI(XI_INPLACE); break;

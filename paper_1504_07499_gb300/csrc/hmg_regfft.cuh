@@ -99,6 +99,7 @@ template <> struct Split<96> { static constexpr int TP = 4, E = 24; };
 template <> struct Split<128> { static constexpr int TP = 8, E = 16; };
 template <> struct Split<192> { static constexpr int TP = 8, E = 24; };
 template <> struct Split<256> { static constexpr int TP = 16, E = 16; };
+template <> struct Split<512> { static constexpr int TP = 16, E = 32; };
 
 // Shared-memory slot of (k1, n2) of one pencil: k1-major with one pad row per group of
 // E/TP k1 values, so that stage-2 readers of different groups fall on different banks.
