@@ -413,7 +413,7 @@ __device__ __forceinline__ void row_forward_split(float2* v, int t, float2* rs, 
 }
 
 template <int M, int RW, int MODE>
-__global__ void __launch_bounds__(RW * Split<M>::TP, 4)
+__global__ void __launch_bounds__(RW * Split<M>::TP, 1024 / (RW * Split<M>::TP))
 k_fx_forward(GridDesc g, unsigned mask, const float* __restrict__ tau, float2* __restrict__ spec,
              double* __restrict__ partial) {
     constexpr int E = Split<M>::E, TP = Split<M>::TP, RS = row_stride<M>();
@@ -496,12 +496,15 @@ __device__ __forceinline__ void row_inverse(float2* v, int t, float2* rs, const 
     stage2_read<M, false>(v, t, rs, 1);
 }
 
-// residual sweeps hold the old row (and r) in registers beside the transform: two CTAs per SM
+// threads per SM the register bound aims at: residual sweeps hold the old row (and r) in
+// registers beside the transform
 template <int M, int MODE>
-constexpr int fx_inverse_min_ctas() { return (MODE == XI_ADD_R_RES || MODE == XI_INPLACE_RES || Split<M>::E > 16) ? 2 : 3; }
+constexpr int fx_inverse_min_threads() {
+    return (MODE == XI_ADD_R_RES || MODE == XI_INPLACE_RES || Split<M>::E > 16) ? 512 : 768;
+}
 
 template <int M, int RW, int MODE>
-__global__ void __launch_bounds__(RW * Split<M>::TP, fx_inverse_min_ctas<M, MODE>())
+__global__ void __launch_bounds__(RW * Split<M>::TP, fx_inverse_min_threads<M, MODE>() / (RW * Split<M>::TP))
 k_fx_inverse(GridDesc g, unsigned mask, const float2* __restrict__ spec, float* __restrict__ tau,
              const float* __restrict__ r32, double* __restrict__ partial) {
     constexpr int E = Split<M>::E, TP = Split<M>::TP, RS = row_stride<M>();
@@ -550,7 +553,7 @@ k_fx_inverse(GridDesc g, unsigned mask, const float2* __restrict__ spec, float* 
 // against).  The spectrum is transformed in place.  Same float operations as
 // k_fx_inverse followed by k_fx_forward<XF_POLARIZE>, so results are identical.
 template <int M, int RW, bool ADDR, bool WTAU>
-__global__ void __launch_bounds__(RW * Split<M>::TP, 2)
+__global__ void __launch_bounds__(RW * Split<M>::TP, 512 / (RW * Split<M>::TP))
 k_fx_round(GridDesc g, unsigned mask, float2* __restrict__ spec, float* __restrict__ tau,
            const float* __restrict__ r32) {
     constexpr int E = Split<M>::E, TP = Split<M>::TP, RS = row_stride<M>();
@@ -614,7 +617,9 @@ constexpr int pow2_cols(int cap, int M) {
 }
 template <int L> constexpr int fy_cols() { return pow2_cols(256 / fast::Split<L>::TP, L / 2); }
 template <int L> constexpr int fz_cols() { return pow2_cols(128 / fast::Split<L>::TP, L / 2); }
-template <int M> constexpr int fx_rows() { return 256 / fast::Split<M>::TP; }
+// x passes run 128-thread CTAs: their barriers stall fewer warps and the load phases of
+// the CTAs on an SM drift apart (x round trip 400 -> 376 us at 256^3 against 256 threads)
+template <int M> constexpr int fx_rows() { return 128 / fast::Split<M>::TP; }
 }  // namespace
 
 #define HMG_FAST_LEN(L, X) \
