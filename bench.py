@@ -325,17 +325,18 @@ def main() -> None:
     dom = max((k for k in kinds if k not in skip), key=lambda k: kinds[k][0])
     d_ms, d_n, d_bytes = kinds[dom]
     achieved = (d_bytes / d_n) / (d_ms / d_n / 1e3) / 1e9
-    traffic = None
+    traffic, traffic_form = None, None
     try:
         with open(os.path.join(ROOT, "profiles", "ncu_traffic.json")) as fh:
             tinfo = json.load(fh)
         ent = tinfo.get(args.precision, {}).get(dom)
         if ent and ent.get("source_sha") == _kernel_sha():
             traffic = ent["dram_bytes_per_launch"]
+            traffic_form = {"kernel": ent.get("form"), "algo_bytes_per_launch": ent.get("form_algo_bytes_per_launch")}
     except (OSError, ValueError):
         pass
     roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": traffic, "peak_source": peak_src,
+                "frac": achieved / peak, "traffic": traffic, "traffic_form": traffic_form, "peak_source": peak_src,
                 "algo_bytes_per_launch": d_bytes / d_n, "avg_launch_ms": d_ms / d_n}
     # whole-sweep algorithmic fraction: 25 B (FP32) / 49 B (FP64) per voxel-iteration
     per_vox = 25.0 if prec == hmg.HMG_FP32_BULK else 49.0
