@@ -47,6 +47,26 @@ def workload_config(precision: str) -> dict:
             "l2": f"inputs larger than L2 (solver fields {state_gb:.1f} GB vs 129 MB L2), no flush"}
 
 
+def replica_seed(rank: int) -> int:
+    """RVE realization of a rank: independent replicas, one RVE per GPU (weak scaling)."""
+    return SEED + rank
+
+
+def job_totals(seconds: float, voxel_iters: float, world: int, device: str = "cuda"):
+    """Whole-job totals of an independent-replica run: the slowest rank's time and the sum
+    of every rank's voxel-iterations.  These two reductions (and the barriers around the
+    timed region) are the only communication; the data path has no collective."""
+    if world == 1:
+        return seconds, voxel_iters
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([seconds], dtype=torch.float64, device=device)
+    v = torch.tensor([voxel_iters], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(v, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(v.item())
+
+
 def measured_peaks() -> dict:
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -223,7 +243,7 @@ def main() -> None:
 
     prec = hmg.HMG_FP32_BULK if args.precision == "fp32bulk" else hmg.HMG_FP64
     ctx = hmg.Context(local)
-    seed = SEED + rank
+    seed = replica_seed(rank)
     sl = I.generate_spheres(seed, N_SPHERES, F_SP)
     sph_d = torch.from_numpy(np.ascontiguousarray(sl.spheres)).cuda()
     phase_d = torch.empty(N_GRID ** 3, dtype=torch.uint8, device="cuda")
@@ -269,15 +289,7 @@ def main() -> None:
     trace = hmg.hmg_trace_read(ctx.handle)
     clocks = sampler.stop()
 
-    tot = torch.tensor([ms, float(sweeps * N3)], dtype=torch.float64, device="cuda")
-    if world > 1:
-        t_max = tot[:1].clone()
-        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
-        vox = tot[1:].clone()
-        dist.all_reduce(vox, op=dist.ReduceOp.SUM)
-        ms_max, vox_all = float(t_max.item()), float(vox.item())
-    else:
-        ms_max, vox_all = ms, float(sweeps * N3)
+    ms_max, vox_all = job_totals(ms, float(sweeps * N3), world)
     value = vox_all / (ms_max / 1e3)
 
     # --- end to end through the C ABI with host buffers ---------------------------
@@ -293,15 +305,7 @@ def main() -> None:
         e2e_sweeps += sum(info["iters"])
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
-    e2e_t = torch.tensor([e2e_s, float(e2e_sweeps * N3)], dtype=torch.float64, device="cuda")
-    if world > 1:
-        a = e2e_t[:1].clone()
-        dist.all_reduce(a, op=dist.ReduceOp.MAX)
-        b = e2e_t[1:].clone()
-        dist.all_reduce(b, op=dist.ReduceOp.SUM)
-        e2e_s, e2e_vox = float(a.item()), float(b.item())
-    else:
-        e2e_vox = float(e2e_sweeps * N3)
+    e2e_s, e2e_vox = job_totals(e2e_s, float(e2e_sweeps * N3), world)
     h2d = sl.spheres.nbytes + N3
     d2h = N3 + 9 * 8
 
