@@ -7,7 +7,7 @@ RSA + growth sweeps), layer l = 0.3, conductivities 0.20 / 0.25 / 400 (contrast 
 
 value  = voxel-iterations/s = sum over steps of N^3 * (sweeps over the 3 gradients) / time,
          inputs resident in HBM, device time from CUDA events around the K timed steps,
-         max over ranks; fields (1.4 GB) are far larger than L2, so no flush is needed.
+         max over ranks; fields (4.2 GB) are far larger than L2, so no flush is needed.
 e2e    = the same metric through the public C ABI with host buffers: the sphere list
          and the phase grid cross host<->device inside every step.
 Multi-GPU: independent replicas (one RVE per rank, seed 3000 + rank), weak scaling.
@@ -39,7 +39,7 @@ UNIT = "voxel-iter/s"
 
 
 def workload_config(precision: str) -> dict:
-    state_gb = 1.4 * (N_GRID / 256) ** 3
+    state_gb = 4.2 * (N_GRID / 256) ** 3    # FP32-bulk state of the three gradients
     return {"workload": f"rsa{N_GRID}: {N_GRID}^3 RVE, 100 spheres at 40% (RSA + growth sweeps), layer 0.3, "
                         "k 0.20/0.25/400 (contrast 2000), tol 1e-8, 3 unit gradients",
             "N": N_GRID, "n_spheres": N_SPHERES, "f_sp": F_SP, "layer": LAYER, "k": list(K_PHASES),
