@@ -187,11 +187,12 @@ def main() -> None:
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison solve")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
-    ap.add_argument("--mode", default="single", choices=["single", "batch", "serve", "contrast", "schemes"],
+    ap.add_argument("--mode", default="single", choices=["single", "batch", "serve", "contrast", "schemes", "layers"],
                     help="single: the 256^3 RVE (default); batch: 64 mixed-size RVEs in one engine; "
                          "serve: Poisson request stream through hmg_submit/hmg_poll; "
                          "contrast: the 256^3 RVE over 4 contrasts x 3 layers, FP32 bulk and FP64; "
-                         "schemes: Eyre-Milton vs the basic scheme at 3 contrasts")
+                         "schemes: Eyre-Milton vs the basic scheme at 3 contrasts; "
+                         "layers: the paper's sweep over the coating layer at 64^3/128^3/256^3")
     ap.add_argument("--requests", type=int, default=48, help="serve mode: requests per arrival rate")
     ap.add_argument("--variant", type=int, default=-1,
                     help="pin the FP32 kernel variant of the 256^3 grid (0..7, see hmg_set_variant); "
@@ -216,6 +217,9 @@ def main() -> None:
         return
     if args.mode == "schemes":
         run_schemes(args)
+        return
+    if args.mode == "layers":
+        run_layers(args)
         return
     if args.mode == "serve":
         run_serve(args)
@@ -580,6 +584,63 @@ def run_schemes(args) -> None:
             "config": {"workload": "rsa256 scheme comparison: 256^3, 100 spheres at 40 % (seed 3000), l = 0.3, "
                                    "k 0.20/0.25/{2,40,400}", "precision": "fp32bulk"},
             "cases": cases}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+
+
+def run_layers(args) -> None:
+    """The paper's sweep over the coating layer (§5): phases matrix 1, inclusion 0.2, coating
+    400 (contrast 2000), spheres at f_sp = 0.3 (coating included), n_sp in {30, 70, 100},
+    l in {0.02, 0.04, 0.06, 0.08, 0.1, 0.2, ..., 0.9}, at 64^3, 128^3 (10 samples per point,
+    seeds 6000 + s) and 256^3 (3 samples), FP32 bulk to tol 1e-8.  Reports the mean and
+    standard deviation over samples of tr K / 3 (the paper's homogenized value), the largest
+    off-diagonal / diagonal ratio, whether tr K / 3 never falls as l grows, for every sample (exact for
+    the discrete problem: a thicker layer only raises voxel conductivities, from 0.2 to 400,
+    and K is monotone in them), and whether the spread shrinks with the resolution."""
+    import torch
+    from paper_1504_07499_gb300 import build, hmg
+    from paper_1504_07499_gb300 import inputs as I
+    build.build()
+    ctx = hmg.Context(0)
+    k = (1.0, 0.2, 400.0)
+    layers = (0.02, 0.04, 0.06, 0.08, 0.1, 0.2, 0.3, 0.4, 0.5, 0.6, 0.7, 0.8, 0.9)
+    plan = ((64, 10), (128, 10), (256, 3))
+    lists = _sphere_lists([(6000 + smp, n, 0.3) for n in (30, 70, 100) for smp in range(10)])
+    sph = {(n, smp): lists[i * 10 + smp] for i, n in enumerate((30, 70, 100)) for smp in range(10)}
+    out, vox, tt, monotone, aniso = {}, 0.0, 0.0, True, 0.0
+    for N, samples in plan:
+        ph = torch.empty(N ** 3, dtype=torch.uint8, device="cuda")
+        for n in (30, 70, 100):
+            traces = np.zeros((samples, len(layers)))
+            for smp in range(samples):
+                sd = torch.from_numpy(np.ascontiguousarray(sph[(n, smp)])).cuda()
+                for j, layer in enumerate(layers):
+                    hmg.hmg_voxelize(ctx.handle, sd, layer, N, ph)
+                    torch.cuda.synchronize()
+                    t = time.perf_counter()
+                    K, info, st = hmg.hmg_solve(ctx.handle, ph, N, k, TOL, hmg.HMG_FP32_BULK)
+                    tt += time.perf_counter() - t
+                    vox += N ** 3 * sum(info["iters"])
+                    d = np.diag(K)
+                    traces[smp, j] = d.mean()
+                    aniso = max(aniso, float(np.abs(K - np.diag(d)).max() / d.mean()))
+                # non-decreasing (equal where the voxelization does not change between two l)
+                monotone &= bool((np.diff(traces[smp]) >= -1e-7 * traces[smp, 1:]).all())
+            out[f"{N}/{n}"] = {"mean": traces.mean(0).tolist(), "std": traces.std(0, ddof=1).tolist(),
+                               "samples": samples}
+        print(json.dumps({"done": N}), file=sys.stderr, flush=True)
+    shrink = [out[f"256/{n}"]["std"][j] < out[f"64/{n}"]["std"][j] for n in (30, 70, 100) for j in range(len(layers))]
+    line = {"metric": "voxel-iterations/s over the paper's layer sweep (64^3, 128^3, 256^3; 3 unit gradients, tol 1e-8)",
+            "value": vox / tt, "unit": UNIT, "n_gpus": 1, "steps": 3 * len(layers) * sum(s for _, s in plan),
+            "warmup": 0, "ms_per_step": 1e3 * tt / (3 * len(layers) * sum(s for _, s in plan)),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "paper layer sweep: k 1/0.2/400, f_sp 0.3, n_sp 30/70/100, l 0.02..0.9, "
+                                   "10 samples at 64^3 and 128^3, 3 at 256^3 (seeds 6000+)", "precision": "fp32bulk",
+                       "layers": list(layers)},
+            "k_mean_over_samples": out, "rises_with_layer_every_sample": monotone,
+            "max_offdiag_over_diag": aniso,
+            "std_256_below_std_64_fraction": sum(shrink) / len(shrink)}
     print(json.dumps(line), flush=True)
     ctx.close()
 
