@@ -741,13 +741,20 @@ def run_serve(args) -> None:
 
 
 def _kernel_sha() -> str:
+    """Hash of the CUDA sources' code (comments and blank lines left out), which ties a
+    stored ncu measurement to the code it was taken on."""
     import hashlib
+    import re
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1504_07499_gb300", "csrc")
     for f in sorted(os.listdir(csrc)):
         if f.endswith((".cu", ".cuh", ".h")):
-            with open(os.path.join(csrc, f), "rb") as fh:
-                h.update(fh.read())
+            with open(os.path.join(csrc, f), encoding="utf-8") as fh:
+                text = re.sub(r"/\*.*?\*/", "", fh.read(), flags=re.S)
+            for line in text.splitlines():
+                code = re.sub(r"//.*", "", line).rstrip()
+                if code:
+                    h.update(code.encode() + b"\n")
     return h.hexdigest()[:16]
 
 

@@ -13,6 +13,8 @@
 // inverse back to the natural layout without an extra exchange).
 // Loads and stores go between HBM and registers with the pencil index fastest across
 // threads, so every warp access is a run of contiguous bytes.
+// Within a block of FP32 sweeps the x inverse of one sweep and the x forward of the next
+// are one kernel (k_fx_round); the y and z passes are the same in every sweep.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -278,7 +280,7 @@ k_fzs(GridDesc g, unsigned mask, float2* __restrict__ spec, double* __restrict__
 }
 
 // ---------------------------------------------------------------------------
-// x passes: R rows per CTA, threads (t, r) with t fastest along the row
+// x passes: RW rows per CTA (128 threads), threads (t, r) with t fastest along the row
 // ---------------------------------------------------------------------------
 
 // Coefficient pairs for two neighbouring voxels of phases (a, b): lut[a | b << 2] = (c_a, c_b).

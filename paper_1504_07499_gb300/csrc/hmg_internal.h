@@ -47,7 +47,7 @@ struct GridDesc {
     int xyvar;             // 1: fused x + y cluster kernels, 0: separate x and y passes (autotuned)
     int nochain;           // 1: FP32 sweeps of a block are not chained through k_fx_round
     // Per-slot flags in device memory (engine launches; nullptr = use the launch's
-    // mask and template modes): SF_ACTIVE, SF_ADDB (add 2 k0 E at DC, plain sweep),
+    // mask and template modes): SF_ACTIVE, SF_ADDB (add gc E at DC, plain sweep),
     // SF_ADDR (add the defect r, correction sweep).  `resid`: this launch of the x
     // inverse also reads the old field and sums the residual (flags mode only).
     const int* dflags;

@@ -10,6 +10,9 @@
 // Y = (k - k0)/(k + k0) and P the projector xi xi^T/|xi|^2 (Gamma0 = -P/k0 for
 // L0 = -k0 I), steps 2-7 read tau^{n+1} = (I - 2P)(Y tau^n) + 2 k0 E, and
 // e^n - e_comp^n = (tau^n - tau^{n+1}) / (2 k0), so no field but tau is stored.
+// (The basic scheme runs through the same passes on e itself, with its own Y and the
+// Green step -P; GridDesc carries the scheme's coefficients.)  These generic kernels
+// serve FP64 and the sizes without register-resident FP32 kernels (hmg_fast.cu).
 //
 // Spectrum layout: after the x pass each row of N reals becomes N/2 complex values
 // (x-major rows, same byte size as the real field); entry kx = 0 packs the two real
@@ -229,8 +232,9 @@ k_y_pass(GridDesc g, unsigned mask, typename Cplx<R>::T* __restrict__ spec) {
 
 // ---------------------------------------------------------------------------
 // z pass: Pz consecutive kx columns at one ky, all three components, length N
-// along z.  Z_ITER: forward, tau_hat <- (I - 2P) tau_hat / N^3 (+ 2 k0 E at DC),
-// inverse.  Z_EQ: forward, then sum |xi . phi_hat|^2 / N^6 in FP64.
+// along z.  Z_ITER: forward, tau_hat <- (ga - gb P) tau_hat / N^3 (+ gc E at DC;
+// Eyre-Milton: (I - 2P) and 2 k0 E), inverse.  Z_EQ: forward, then sum
+// |xi . phi_hat|^2 / N^6 in FP64.
 // ---------------------------------------------------------------------------
 
 template <typename R, int MODE>
