@@ -32,3 +32,22 @@ def test_workload_record():
     cfg = bench.workload_config("fp32bulk")
     assert cfg["N"] == bench.N_GRID == 256 and cfg["workload"].startswith("rsa256")
     assert cfg["k"] == list(bench.K_PHASES) and cfg["tol"] == 1e-8
+
+
+def test_torch_fft_comparison_sweep_matches_the_oracle():
+    """The cuFFT comparison leg's sweep, run here on the CPU, against one oracle sweep."""
+    import numpy as np
+    import pytest
+    torch = pytest.importorskip("torch")
+    from oracle import em as om
+    from paper_1504_07499_gb300 import inputs as I
+    N, k = 16, I.K_PHASES
+    ph = om.voxelize(I.generate_spheres(7, 10, 0.3).spheres, 0.3, N)
+    k0 = om.reference_k0(k)
+    for E in ((1.0, 0.0, 0.0), (0.0, 0.0, 1.0)):
+        ref = om.em_solve(ph, k, E, tol=0.0, max_iter=1, record=True)
+        sweep = bench.torch_fft_sweep(torch.from_numpy(ph.reshape(-1)), k, N, "cpu")
+        kp = torch.tensor(np.asarray(k) + k0, dtype=torch.float32)[torch.from_numpy(ph).long()]
+        tau0 = kp[None] * torch.tensor(E, dtype=torch.float32)[:, None, None, None]
+        e1 = (sweep(tau0, E) / kp[None]).double().numpy()
+        assert np.abs(e1 - ref.e).max() < 1e-5 * np.abs(ref.e).max()
