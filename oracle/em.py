@@ -19,8 +19,9 @@ Everything here is plain FP64 numpy written from the paper:
 * §3 (the list of FFT-based schemes) and eqs. 1-3: the basic scheme, the plain
   fixed-point iteration of the Lippmann-Schwinger equation (``basic_solve``).
 
-The 3D DFT is either a direct sum (``dft3_direct``, small grids) or the library
-FFT (scipy.fft), which the tests pin against the direct sum.
+The 3D DFT is the direct sum (``dft3_direct``, taken axis by axis) on grids up to
+16^3, and the library FFT (scipy.fft) above that, which the tests pin against the
+direct sum.
 
 Readings where the paper is silent or garbled (each is also listed in the design
 notes):
@@ -157,8 +158,9 @@ def _dft_matrix(N: int) -> np.ndarray:
     return _DFT_CACHE[N]
 
 
-def dft3_direct(x: np.ndarray, inverse: bool = False) -> np.ndarray:
-    """Unnormalized 3D DFT by the direct sum (inverse: conjugate kernel, no 1/N^3)."""
+def dft3_dense(x: np.ndarray, inverse: bool = False) -> np.ndarray:
+    """Unnormalized 3D DFT as one dense N^3 x N^3 matrix product (the definition
+    written out; meant for N <= 8, where it pins ``dft3_direct``)."""
     N = x.shape[-1]
     M = _dft_matrix(N)
     flat = x.reshape(x.shape[:-3] + (N ** 3,)).astype(np.complex128)
@@ -166,23 +168,42 @@ def dft3_direct(x: np.ndarray, inverse: bool = False) -> np.ndarray:
     return y.reshape(x.shape)
 
 
+def dft3_direct(x: np.ndarray, inverse: bool = False) -> np.ndarray:
+    """Unnormalized 3D DFT by the direct sum (inverse: conjugate kernel, no 1/N^3).
+    exp(-2 pi i k.n/N) factors into one exponential per axis, so the triple sum is
+    taken one axis at a time with the N x N matrix W[k, n] = exp(-+2 pi i (k n mod N)/N):
+    O(N^4) work, no fast algorithm."""
+    N = x.shape[-1]
+    kn = np.outer(np.arange(N), np.arange(N)) % N
+    W = np.exp((2j if inverse else -2j) * np.pi * kn / N)
+    y = x.astype(np.complex128)
+    for axis in (-1, -2, -3):
+        y = np.moveaxis(np.tensordot(y, W, axes=([axis], [1])), -1, axis)
+    return y
+
+
 def _workers() -> int:
     return int(os.environ.get("HMG_ORACLE_THREADS", os.cpu_count() or 1))
 
 
 def fft3(x: np.ndarray) -> np.ndarray:
-    """Unnormalized forward 3D DFT over the last three axes."""
+    """Unnormalized forward 3D DFT over the last three axes: the direct sum on grids up
+    to 16^3, the library FFT above (pinned against the direct sum in the tests)."""
     N = x.shape[-1]
-    if N <= 8 or _sfft is None:
-        return dft3_direct(x) if N <= 16 else np.fft.fftn(x, axes=(-3, -2, -1))
+    if N <= 16:
+        return dft3_direct(x)
+    if _sfft is None:
+        return np.fft.fftn(x, axes=(-3, -2, -1))
     return _sfft.fftn(x, axes=(-3, -2, -1), workers=_workers())
 
 
 def ifft3_unnorm(X: np.ndarray) -> np.ndarray:
     """Unnormalized inverse 3D DFT (kernel exp(+2 pi i k.n/N), no 1/N^3)."""
     N = X.shape[-1]
-    if N <= 8 or _sfft is None:
-        return dft3_direct(X, inverse=True) if N <= 16 else np.fft.ifftn(X, axes=(-3, -2, -1)) * N ** 3
+    if N <= 16:
+        return dft3_direct(X, inverse=True)
+    if _sfft is None:
+        return np.fft.ifftn(X, axes=(-3, -2, -1)) * N ** 3
     return _sfft.ifftn(X, axes=(-3, -2, -1), workers=_workers(), norm="forward")
 
 
@@ -251,6 +272,12 @@ def equilibrium_residual(k_field: np.ndarray, e: np.ndarray, xi: np.ndarray):
     return math.sqrt(float((np.abs(div) ** 2).sum())) / float(np.linalg.norm(mean)), mean
 
 
+def compatibility_residual(e: np.ndarray, ec: np.ndarray, normE: float) -> float:
+    """Step 6: eps_comp = sqrt(<|e - e_comp|^2>) / |grad Theta|, the volume average
+    <.> being the mean over the N^3 voxels."""
+    return math.sqrt(float(((e - ec) ** 2).sum(0).mean())) / normE
+
+
 def em_solve(phase: np.ndarray, k_phases, grad_Theta, tol: float = 1e-8,
              max_iter: int = 20000, record: bool = False, e0: np.ndarray | None = None) -> EMResult:
     """Eyre-Milton accelerated scheme of §3 (Algorithm, steps 1-7) for one macroscopic
@@ -284,7 +311,7 @@ def em_solve(phase: np.ndarray, k_phases, grad_Theta, tol: float = 1e-8,
         ec_c = ifft3_unnorm(ec_hat) / N ** 3
         ec = ec_c.real
         # Step 6: eps_comp = sqrt(<|e - e_comp|^2>) / |grad Theta|.
-        eps_comp = math.sqrt(float(((e - ec) ** 2).sum(0).mean())) / normE
+        eps_comp = compatibility_residual(e, ec, normE)
         if record:
             hist_c.append(eps_comp)
         if not math.isfinite(eps_comp):
@@ -355,7 +382,7 @@ def basic_solve(phase: np.ndarray, k_phases, grad_Theta, tol: float = 1e-8,
         ec_hat[:, 0, 0, 0] = E * N ** 3
         ec = (ifft3_unnorm(ec_hat) / N ** 3).real
         # Step 6: eps_comp = sqrt(<|e - e_comp|^2>) / |grad Theta|.
-        eps_comp = math.sqrt(float(((e - ec) ** 2).sum(0).mean())) / normE
+        eps_comp = compatibility_residual(e, ec, normE)
         if record:
             hist_c.append(eps_comp)
         if not math.isfinite(eps_comp):
