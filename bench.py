@@ -96,6 +96,13 @@ def torch_fft_sweep(phase, k, N: int, device):
     return sweep
 
 
+def k_entry_err(K, Kref, floor_frac: float = 1e-2) -> float:
+    """Largest relative error over the entries of K; entries below floor_frac times the
+    largest diagonal entry of Kref are compared with that floor."""
+    floor = floor_frac * float(np.abs(np.diag(Kref)).max())
+    return float((np.abs(np.asarray(K) - Kref) / np.maximum(np.abs(Kref), floor)).max())
+
+
 def measured_peaks() -> dict:
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -285,8 +292,8 @@ def main() -> None:
 
     def step():
         hmg.hmg_voxelize(ctx.handle, sph_d, LAYER, N_GRID, phase_d)
-        _, info, _ = hmg.hmg_solve(ctx.handle, phase_d, N_GRID, K_PHASES, TOL, prec)
-        return info
+        K, info, _ = hmg.hmg_solve(ctx.handle, phase_d, N_GRID, K_PHASES, TOL, prec)
+        return K, info
 
     if args.variant >= 0:
         hmg.hmg_set_variant(ctx.handle, N_GRID, args.variant)
@@ -304,24 +311,31 @@ def main() -> None:
 
     sampler = ClockSampler(local)
     sampler.start()
-    hmg.hmg_trace_enable(ctx.handle, True)
     barrier()
     torch.cuda.synchronize()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record()
-    sweeps, lat = 0, []
+    sweeps, lat, Ks = 0, [], []
     for _ in range(args.steps):
         t = time.perf_counter()
-        info = step()
+        K_step, info = step()
         lat.append(time.perf_counter() - t)
         sweeps += sum(info["iters"])
+        Ks.append(K_step)
     ev1.record()
     torch.cuda.synchronize()
     barrier()
     ms = ev0.elapsed_time(ev1)
+    clocks = sampler.stop()
+    # kernel breakdown from one more solve of the same RVE, outside the timed region, with
+    # the library's tracer on (CUDA events on the launching stream around every launch);
+    # a solve launches the same kernels every time, so its launch count per step holds
+    # for the timed steps too
+    hmg.hmg_trace_enable(ctx.handle, True)
+    _, info_tr = step()
     hmg.hmg_trace_enable(ctx.handle, False)
     trace = hmg.hmg_trace_read(ctx.handle)
-    clocks = sampler.stop()
+    assert list(info_tr["iters"]) == list(info["iters"]), "traced solve took other sweep counts"
 
     ms_max, vox_all = job_totals(ms, float(sweeps * N3), world)
     value = vox_all / (ms_max / 1e3)
@@ -362,7 +376,13 @@ def main() -> None:
     skip = ("other", "fp64") if args.precision == "fp32bulk" else ("other",)
     dom = max((k for k in kinds if k not in skip), key=lambda k: kinds[k][0])
     d_ms, d_n, d_bytes = kinds[dom]
-    achieved = (d_bytes / d_n) / (d_ms / d_n / 1e3) / 1e9
+    launch_s = d_ms / d_n / 1e3
+    # algorithmic bytes per launch: 25 B (FP32) / 49 B (FP64) per voxel-iteration and
+    # gradient -- read the field and the phase id, write the field -- times the voxels
+    # of the three gradients one launch processes
+    per_vox = 25.0 if prec == hmg.HMG_FP32_BULK else 49.0
+    algo_bytes = per_vox * 3 * N3
+    achieved = algo_bytes / launch_s / 1e9
     traffic, traffic_form = None, None
     try:
         with open(os.path.join(ROOT, "profiles", "ncu_traffic.json")) as fh:
@@ -374,14 +394,32 @@ def main() -> None:
     except (OSError, ValueError):
         pass
     roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": traffic, "traffic_form": traffic_form, "peak_source": peak_src,
-                "algo_bytes_per_launch": d_bytes / d_n, "avg_launch_ms": d_ms / d_n}
-    # whole-sweep algorithmic fraction: 25 B (FP32) / 49 B (FP64) per voxel-iteration
-    per_vox = 25.0 if prec == hmg.HMG_FP32_BULK else 49.0
+                "frac": achieved / peak, "traffic": traffic, "peak_source": peak_src,
+                "algo_bytes_per_launch": algo_bytes, "algo_bytes_per_unit": per_vox,
+                "units_per_launch": 3 * N3, "avg_launch_ms": d_ms / d_n,
+                # the bytes this kernel's form moves (the x round trip also reads the
+                # correction right-hand side or stores the field in some launches)
+                "form_bytes_per_launch": d_bytes / d_n,
+                "form_frac": (d_bytes / d_n) / launch_s / 1e9 / peak,
+                "dram_frac": (traffic / launch_s / 1e9 / peak) if traffic else None,
+                "traffic_form": traffic_form}
     kernels = {k: {"ms": v[0], "launches": v[1], "share": v[0] / total_ms,
                    "GBps": (v[2] / (v[0] / 1e3) / 1e9) if v[0] > 0 and v[2] > 0 else None}
                for k, v in kinds.items()}
     launches = int(sum(v[1] for v in kinds.values()))
+
+    # accuracy of the timed solves: K against the oracle's stored result for this RVE
+    # (FP64, written offline from the oracle alone) when there is one
+    k_check = {}
+    try:
+        with open(os.path.join(ROOT, "tests", "golden", f"oracle_rsa{N_GRID}_s{seed}.json")) as fh:
+            ref = json.load(fh)
+        if ref["params"]["layer"] == LAYER and tuple(ref["params"]["k"]) == K_PHASES and ref["params"]["tol"] == TOL:
+            Kref = np.array(ref["K"])
+            k_check = {"k_err_vs_oracle": max(k_entry_err(Kk, Kref) for Kk in Ks),
+                       "oracle_fp64_sweeps": int(sum(ref["iters"]))}
+    except (OSError, ValueError, KeyError):
+        pass
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
@@ -391,21 +429,31 @@ def main() -> None:
             "solves_per_s": world * args.steps / (ms_max / 1e3),
             "latency_ms": {"p50": 1e3 * float(np.percentile(lat, 50)), "p99": 1e3 * float(np.percentile(lat, 99))},
             "sweeps_per_solve": sweeps / args.steps,
+            "accuracy": {"k_err_definition": "max over entries of |K - Kref| / max(|Kref_ij|, 0.01 max_i Kref_ii)",
+                         **k_check},
             "roofline": roofline,
             "algorithmic_hbm_frac": value / world * per_vox / (peak * 1e9),
             "kernels": kernels,
-            "gpu_launches": launches,
+            "gpu_launches": launches * args.steps,
+            "gpu_launches_note": "launches of one traced solve of the same RVE (outside the timed region) x steps",
             "z_variant": hmg.hmg_get_variant(ctx.handle, N_GRID),
             "clocks": clocks,
             "e2e": {"value": e2e_vox / e2e_s if e2e_vox else None, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}}
 
     if not args.no_fp64 and prec == hmg.HMG_FP32_BULK:
         t = time.perf_counter()
-        _, info64, _ = hmg.hmg_solve(ctx.handle, phase_d, N_GRID, K_PHASES, TOL, hmg.HMG_FP64)
+        K64, info64, _ = hmg.hmg_solve(ctx.handle, phase_d, N_GRID, K_PHASES, TOL, hmg.HMG_FP64)
         dt = time.perf_counter() - t
         sw = sum(info64["iters"])
         line["fp64_plain"] = {"voxel_iter_per_s": sw * N3 / dt, "solve_s": dt, "sweeps": sw,
                               "speedup_fp32bulk_solves": dt / (ms_max / 1e3 / args.steps)}
+        line["accuracy"]["k_err_vs_gpu_fp64"] = max(k_entry_err(Kk, K64) for Kk in Ks)
+    # work-to-solution: voxel-iterations counted on the plain FP64 method's sweep count
+    # (FP32 bulk runs more sweeps than FP64 to reach the same FP64 residuals)
+    ref_sweeps = line["accuracy"].get("oracle_fp64_sweeps") or line.get("fp64_plain", {}).get("sweeps")
+    if ref_sweeps:
+        line["effective_voxel_iter_per_s"] = world * args.steps * ref_sweeps * N3 / (ms_max / 1e3)
+        line["effective_note"] = "N^3 x (FP64 sweeps of the same RVE) per solve / solve time"
     if not args.no_cufft and prec == hmg.HMG_FP32_BULK:
         # comparison point: the same tau-form sweep on torch.fft (cuFFT) + torch pointwise ops
         sweep = torch_fft_sweep(phase_d, K_PHASES, N_GRID, "cuda")

@@ -199,16 +199,20 @@ hmg_status hmg_fft_inverse(hmg_ctx* ctx, int N, int count, hmg_precision precisi
  * and calls no cudaMalloc, cudaFree or allocating library routine: its scratch (about
  * 13 MB: the field, the packed spectrum, partial sums and the twiddle table of one
  * N <= HMG_NOALLOC_MAX_N grid) is a set of static device arrays that every GPU which
- * loads libhmg holds until the process exits.
+ * loads libhmg holds until the process exits (the CUDA driver maps them in with the
+ * library's code, not this call).
  * Same arithmetic as hmg_equilibrium with precision HMG_FP64: phase (N^3 bytes) and e
  * (3 N^3 doubles) may be host or device pointers of the current device;
  * eps_eq_out (1 double) and flux_mean_out (NULL or 3 doubles, <k e>) are host memory.
  * Work runs on the current device's legacy default stream and the call returns when
- * it has finished.  The first call on a device looks up the arrays' device addresses
- * (cudaGetSymbolAddress) and caches them; make that first call before any stream
- * capture.  All calls share the arrays, which keep the last call's contents (the
- * sums are cleared at the start of every call): calls that overlap on the GPU, from
- * several host threads or processes sharing a context, race with each other.
+ * it has finished.  Every call looks up the arrays' device addresses in the current
+ * context (cudaGetSymbolAddress) and rewrites the twiddle table and the sums it
+ * uses, so it also works after cudaDeviceReset.  All calls share the arrays, which
+ * keep the last call's contents: two calls overlapping on the GPU would race, so the
+ * library serializes them (a lock held until the call's GPU work has finished).  Work
+ * the caller runs on other streams is not ordered against this call (the legacy
+ * default stream does not wait for non-blocking streams): finish writing phase and e
+ * before the call.
  * Errors: HMG_INVALID_ARG for N > HMG_NOALLOC_MAX_N (or any argument hmg_equilibrium
  * rejects), HMG_CUDA_ERROR if a CUDA call fails. */
 hmg_status hmg_equilibrium_noalloc(const uint8_t* phase, int N, double k_matrix,
@@ -233,6 +237,11 @@ hmg_status hmg_solve_batch(hmg_ctx* ctx, int count, const uint8_t* const* phases
  * queued ones while their footprint (hmg_footprint) fits the context's budget, up to
  * 64 at once; every tick advances all admitted HMG_FP32_BULK requests together in one
  * CUDA-graph launch (continuous batching).  HMG_FP64 requests run one at a time.
+ * The loop and the caller's context share one budget: the first hmg_submit on a
+ * context releases the context's own solve state, and device memory that later calls
+ * on the context hold counts against the loop's admissions (a request that cannot get
+ * its state then finishes with HMG_OUT_OF_MEMORY).  The first hmg_submit starts the
+ * loop; concurrent first calls start one loop.
  * *ticket identifies the request.
  * Returns HMG_BUSY when the queue is full, HMG_INVALID_ARG for bad arguments, and
  * HMG_OUT_OF_MEMORY when the request alone exceeds the budget. */

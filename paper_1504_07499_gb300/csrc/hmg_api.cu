@@ -252,13 +252,17 @@ int autotune_z(::hmg_ctx* c, GridDesc g, SolveState* s, cudaStream_t st) {
 
 void* hmg_ctx::alloc(size_t bytes) {
     if (bytes == 0) return nullptr;
-    if (budget && used + bytes > budget) return nullptr;
+    // reserve the bytes in the (possibly shared) budget first
+    size_t cur = pool->used.load();
+    do {
+        if (pool->limit && cur + bytes > pool->limit) return nullptr;
+    } while (!pool->used.compare_exchange_weak(cur, cur + bytes));
     void* p = nullptr;
     if (cudaMalloc(&p, bytes) != cudaSuccess) {
         cudaGetLastError();
+        pool->used -= bytes;
         return nullptr;
     }
-    used += bytes;
     sizes[p] = bytes;
     return p;
 }
@@ -267,7 +271,7 @@ void hmg_ctx::release(void* p) {
     if (!p) return;
     auto it = sizes.find(p);
     if (it != sizes.end()) {
-        used -= it->second;
+        pool->used -= it->second;
         sizes.erase(it);
     }
     cudaFree(p);

@@ -16,19 +16,6 @@ using namespace hmg;
 
 namespace {
 
-struct DeviceGuard {
-    int prev = -1;
-    explicit DeviceGuard(int dev) {
-        cudaGetDevice(&prev);
-        if (prev != dev) cudaSetDevice(dev);
-    }
-    ~DeviceGuard() {
-        int cur = -1;
-        cudaGetDevice(&cur);
-        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
-    }
-};
-
 hmg_status cuda_status(cudaError_t e, const char* what) {
     if (e == cudaSuccess) return HMG_OK;
     set_error("%s: %s", what, cudaGetErrorString(e));
@@ -122,6 +109,8 @@ hmg_status hmg_create(hmg_ctx** out, int device, size_t budget) {
     size_t fr = 0, tot = 0;
     cudaMemGetInfo(&fr, &tot);
     c->budget = budget ? budget : (size_t)(0.9 * (double)fr);
+    c->pool = std::make_shared<BudgetPool>();
+    c->pool->limit = c->budget;
     *out = c;
     return HMG_OK;
 }
@@ -131,9 +120,12 @@ hmg_status hmg_destroy(hmg_ctx* ctx) {
     if (!ctx) return HMG_OK;
     {
         DeviceGuard dg(ctx->device);
-        if (ctx->server) {
-            delete ctx->server;
-            ctx->server = nullptr;
+        {
+            std::lock_guard<std::mutex> lk(ctx->server_mu);
+            if (ctx->server) {
+                delete ctx->server;
+                ctx->server = nullptr;
+            }
         }
         cudaStreamSynchronize(ctx->stream);
         ctx->solve.free_all(ctx);

@@ -4,10 +4,13 @@
 // nothing (no cudaMalloc, cudaFree, stream or event creation).
 //
 // In host code the names of these arrays are host-side stand-ins, not device
-// addresses: the device addresses are obtained with cudaGetSymbolAddress once per
-// device, on the first call made with that device current, and cached.
-// All calls share the arrays (they keep the last call's contents), so calls that
-// overlap on the GPU race with each other.
+// addresses.  Every call looks their device addresses up with cudaGetSymbolAddress
+// while the caller's device is current (a lookup that allocates nothing), so no
+// address outlives the context it belongs to (cudaDeviceReset, a new primary
+// context), and it writes the twiddle table of its N before using it.
+// All calls share the arrays, which keep the last call's contents; the library
+// serializes its calls (a lock held until the call's GPU work has finished), since
+// two calls overlapping on the GPU would race on them.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -30,7 +33,6 @@ namespace {
 constexpr int kMaxN = HMG_NOALLOC_MAX_N;
 constexpr long long kMaxN3 = (long long)kMaxN * kMaxN * kMaxN;
 constexpr int kMaxPartials = 3 * kMaxN * kMaxN;   // >= CTAs of any pass at N <= kMaxN
-constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) uint8_t g_phase[kMaxN3];
 static __device__ __align__(256) double g_field[3 * kMaxN3];        // e, then the packed spectrum
@@ -40,18 +42,15 @@ static __device__ __align__(256) double g_red[64];
 static __device__ __align__(256) double2 g_tw[kMaxN + kMaxN / 2];
 
 struct Addrs {
-    bool ready = false;
     uint8_t* phase = nullptr;
     double* field = nullptr;
     double* spec = nullptr;
     double* partial = nullptr;
     double* red = nullptr;
     double2* tw = nullptr;
-    int tw_N = 0;          // grid size the twiddle table currently holds
 };
 
 std::mutex g_mu;
-Addrs g_addr[kMaxDevices];
 
 template <typename T>
 bool symbol_address(T** out, const T& sym) {
@@ -61,21 +60,17 @@ bool symbol_address(T** out, const T& sym) {
     return true;
 }
 
-// Once per device, with that device current: look up the arrays' device addresses.
-hmg_status setup(int dev, Addrs** out) {
-    Addrs& a = g_addr[dev];
-    if (!a.ready) {
-        bool ok = symbol_address(&a.phase, g_phase[0]) && symbol_address(&a.field, g_field[0]) &&
-                  symbol_address(&a.spec, g_spec[0]) && symbol_address(&a.partial, g_partial[0]) &&
-                  symbol_address(&a.red, g_red[0]) && symbol_address(&a.tw, g_tw[0]);
-        if (!ok) {
-            cudaError_t e = cudaGetLastError();
-            set_error("cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
-            return HMG_CUDA_ERROR;
-        }
-        a.ready = true;
+// With the caller's device current: the device addresses of the static arrays in the
+// current context.
+hmg_status lookup(Addrs* a) {
+    bool ok = symbol_address(&a->phase, g_phase[0]) && symbol_address(&a->field, g_field[0]) &&
+              symbol_address(&a->spec, g_spec[0]) && symbol_address(&a->partial, g_partial[0]) &&
+              symbol_address(&a->red, g_red[0]) && symbol_address(&a->tw, g_tw[0]);
+    if (!ok) {
+        cudaError_t e = cudaGetLastError();
+        set_error("cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
+        return HMG_CUDA_ERROR;
     }
-    *out = &a;
     return HMG_OK;
 }
 
@@ -106,17 +101,12 @@ extern "C" hmg_status hmg_equilibrium_noalloc(const uint8_t* phase, int N, doubl
             set_error("conductivities must be finite and positive");
             return HMG_INVALID_ARG;
         }
-    int dev = 0;
-    cudaError_t ce = cudaGetDevice(&dev);
-    if (ce != cudaSuccess) return cuda_fail(ce, "cudaGetDevice");
-    if (dev < 0 || dev >= kMaxDevices) {
-        set_error("device %d out of range", dev);
-        return HMG_INVALID_ARG;
-    }
     std::lock_guard<std::mutex> lk(g_mu);
-    Addrs* a = nullptr;
-    hmg_status st = setup(dev, &a);
+    Addrs addrs;
+    Addrs* a = &addrs;
+    hmg_status st = lookup(a);
     if (st != HMG_OK) return st;
+    cudaError_t ce = cudaSuccess;
 
     const cudaStream_t s = 0;   // legacy default stream of the current device
     const long long N3 = (long long)N * N * N;
@@ -129,7 +119,7 @@ extern "C" hmg_status hmg_equilibrium_noalloc(const uint8_t* phase, int N, doubl
     make_plan(M, &gp.pM);
     gp.pN.tw_off = 0;
     gp.pM.tw_off = N;
-    if (a->tw_N != N) {
+    {
         double2 h[kMaxN + kMaxN / 2];
         for (int part = 0; part < 2; ++part) {
             const int L = part == 0 ? N : M, off = part == 0 ? 0 : N;
@@ -144,9 +134,9 @@ extern "C" hmg_status hmg_equilibrium_noalloc(const uint8_t* phase, int N, doubl
                 h[off + k] = make_double2(c, sn);
             }
         }
-        ce = cudaMemcpy(a->tw, h, sizeof(double2) * (N + M), cudaMemcpyHostToDevice);
+        // pageable source: the copy has read h when the call returns
+        ce = cudaMemcpyAsync(a->tw, h, sizeof(double2) * (N + M), cudaMemcpyHostToDevice, s);
         if (ce != cudaSuccess) return cuda_fail(ce, "twiddle upload");
-        a->tw_N = N;
     }
 
     // inputs into the static arrays (host or device sources)

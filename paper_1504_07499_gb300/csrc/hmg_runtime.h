@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <map>
 #include <memory>
 #include <mutex>
@@ -23,6 +24,20 @@ bool is_device_ptr(const void* p);
 cudaError_t copy_in(void* dst_dev, const void* src, size_t bytes, cudaStream_t st);
 cudaError_t copy_out(void* dst, const void* src_dev, size_t bytes, cudaStream_t st);
 size_t state_bytes(int N, bool fp64, int nslots);
+
+// Makes `dev` current for a scope and restores the caller's device afterwards.
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        cudaGetDevice(&prev);
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+    }
+};
 
 // FFT schedules and twiddle tables of one grid size.
 struct GridPlan {
@@ -124,14 +139,21 @@ struct Solver {
 struct Request;
 struct Server;
 
+// Device-memory budget of a context, shared with the request loop's internal context
+// (hmg_submit) so that the two together stay within the caller's budget.
+struct BudgetPool {
+    size_t limit = 0;                 // 0: no limit
+    std::atomic<size_t> used{0};
+};
+
 }  // namespace hmg
 
 struct hmg_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
     cudaStream_t stream64 = nullptr;   // FP64 work overlapped with the FP32 sweeps
-    size_t budget = 0;
-    size_t used = 0;
+    size_t budget = 0;                 // pool->limit
+    std::shared_ptr<hmg::BudgetPool> pool;
     std::map<void*, size_t> sizes;
     std::map<int, std::shared_ptr<hmg::GridPlan>> plans;
     hmg::SolveState solve;
@@ -139,6 +161,7 @@ struct hmg_ctx {
     void* alloc(size_t bytes);
     void release(void* p);
     hmg::Server* server = nullptr;
+    std::mutex server_mu;              // guards the creation of `server`
     hmg::Tracer tracer;
     std::map<int, int> ztune;   // autotuned z-pass variant per grid size (FP32 path)
 };

@@ -17,7 +17,9 @@ static double now_s() {
     return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
 }
 
-Server::Server(int dev, size_t bud) : device(dev), budget(bud) { worker = std::thread([this] { loop(); }); }
+Server::Server(int dev, std::shared_ptr<BudgetPool> p) : device(dev), pool(std::move(p)) {
+    worker = std::thread([this] { loop(); });
+}
 
 Server::~Server() {
     {
@@ -92,9 +94,10 @@ void Server::stats(long long out[6]) {
 
 void Server::loop() {
     hmg_ctx* ctx = nullptr;
-    hmg_status cs = hmg_create(&ctx, device, budget);
+    hmg_status cs = hmg_create(&ctx, device, pool->limit);
     std::unique_ptr<Engine> eng;
     if (cs == HMG_OK) {
+        ctx->pool = pool;   // one budget for the caller's context and this loop
         cudaSetDevice(device);
         eng = std::make_unique<Engine>(ctx, ctx->stream, ctx->stream64, true);
     }
@@ -105,7 +108,8 @@ void Server::loop() {
             std::unique_lock<std::mutex> lk(mu);
             cv.wait(lk, [&] { return stop || !queue.empty() || !running.empty(); });
             if (stop) break;
-            size_t used = eng ? eng->bytes_in_use() : 0;
+            // device memory held by the caller's context and by this loop together
+            size_t used = pool->used.load();
             while (!queue.empty()) {
                 Request& r = reqs[queue.front()];
                 if (r.prec == HMG_FP64) {
@@ -118,7 +122,7 @@ void Server::loop() {
                 if ((int)running.size() + (int)admit.size() >= max_slots) break;
                 // the first request of an idle loop is always admitted (it fits the budget
                 // by the check in hmg_submit); later ones while their footprint fits
-                if ((!running.empty() || !admit.empty()) && used + need > (size_t)(0.95 * (double)budget)) break;
+                if ((!running.empty() || !admit.empty()) && used + need > (size_t)(0.95 * (double)pool->limit)) break;
                 used += need;
                 admit.push_back(r.ticket);
                 queue.pop_front();
@@ -153,10 +157,12 @@ void Server::loop() {
             }
             Entry* e = nullptr;
             hmg_status s = cs != HMG_OK ? cs : eng->add((long long)t, r->phase.data(), r->N, r->k, r->tol, 0, &e);
-            if (s != HMG_OK) {
+            if (s != HMG_OK) {   // e.g. the caller's own solves hold the budget
                 std::lock_guard<std::mutex> lk(mu);
                 r->status = s;
                 r->t_done = now_s();
+                r->info.seconds = r->t_done - r->t_submit;
+                ++n_completed;
                 continue;
             }
             running[e] = t;
@@ -216,9 +222,20 @@ hmg_status hmg_submit(hmg_ctx* ctx, const uint8_t* phase, int N, double km, doub
         set_error("request footprint exceeds the context budget");
         return HMG_OUT_OF_MEMORY;
     }
-    if (!ctx->server) ctx->server = new Server(ctx->device, ctx->budget);
+    Server* srv;
+    {
+        std::lock_guard<std::mutex> lk(ctx->server_mu);
+        if (!ctx->server) {
+            // the caller's solve state is released: the loop's requests draw on the same budget
+            DeviceGuard dg(ctx->device);
+            cudaStreamSynchronize(ctx->stream);
+            ctx->solve.free_all(ctx);
+            ctx->server = new Server(ctx->device, ctx->pool);
+        }
+        srv = ctx->server;
+    }
     const double k[3] = {km, ki, kc};
-    return ctx->server->submit(phase, N, k, tol, precision, ticket);
+    return srv->submit(phase, N, k, tol, precision, ticket);
 }
 
 hmg_status hmg_server_stats(hmg_ctx* ctx, long long out[6]) {
@@ -228,6 +245,7 @@ hmg_status hmg_server_stats(hmg_ctx* ctx, long long out[6]) {
         return HMG_INVALID_ARG;
     }
     for (int i = 0; i < 6; ++i) out[i] = 0;
+    std::lock_guard<std::mutex> lk(ctx->server_mu);
     if (ctx->server) ctx->server->stats(out);
     return HMG_OK;
 }
@@ -238,11 +256,16 @@ hmg_status hmg_poll(hmg_ctx* ctx, uint64_t ticket, double K_out[9], hmg_info* in
         set_error("bad poll arguments");
         return HMG_INVALID_ARG;
     }
-    if (!ctx->server) {
+    Server* srv;
+    {
+        std::lock_guard<std::mutex> lk(ctx->server_mu);
+        srv = ctx->server;
+    }
+    if (!srv) {
         set_error("unknown ticket");
         return HMG_UNKNOWN_TICKET;
     }
-    return ctx->server->poll(ticket, K_out, info);
+    return srv->poll(ticket, K_out, info);
 }
 
 hmg_status hmg_solve_batch(hmg_ctx* ctx, int count, const uint8_t* const* phases, const int* N_list,

@@ -4,11 +4,13 @@
 #include <condition_variable>
 #include <deque>
 #include <map>
+#include <memory>
 #include <mutex>
 #include <thread>
 #include <vector>
 
 #include "../../include/hmg.h"
+#include "hmg_runtime.h"
 
 namespace hmg {
 
@@ -27,7 +29,8 @@ struct Request {
 };
 
 struct Server {
-    explicit Server(int device, size_t budget);
+    // The loop's own context draws on `pool`, the budget of the caller's context.
+    Server(int device, std::shared_ptr<BudgetPool> pool);
     ~Server();
     hmg_status submit(const uint8_t* phase, int N, const double k[3], double tol, hmg_precision p, uint64_t* ticket);
     hmg_status poll(uint64_t ticket, double K[9], hmg_info* info);
@@ -38,7 +41,7 @@ struct Server {
    private:
     void loop();
     int device;
-    size_t budget;
+    std::shared_ptr<BudgetPool> pool;
     int max_slots = 64;
     std::mutex mu;
     std::condition_variable cv;

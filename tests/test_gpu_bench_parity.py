@@ -1,0 +1,129 @@
+"""The benchmark's own configuration against the oracle.
+
+* The 256^3 RVE of the benchmark (100 spheres at 40 %, seed 3000, l = 0.3, contrast
+  2000) and the same spheres on 192^3: eight FP32-bulk sweeps through hmg_solve_fields,
+  so the chained x kernels that dominate the benchmark (x inverse + update + next
+  polarization + x forward in one launch) run on every voxel; every voxel of the
+  three gradient fields against the oracle's eight sweeps at 1e-5 of the largest value.
+* The converged K of the benchmark RVE against the oracle's stored result
+  (tests/golden/oracle_rsa256_s3000.json), FP32 bulk at 1e-5 per entry, FP64 at 1e-9
+  with the oracle's sweep counts (+-1).
+* Contrast 2e4 (coating conductivity 4000, the top of the contrast sweep) on a 64^3
+  grid of the same spheres against tests/golden/oracle_rsa64_s3000_c2e4.json.
+* The 32^3 centred coated sphere (r_s = 0.25, l = 0.25, FP64): K isotropic and equal to
+  the oracle's (tests/golden/oracle_sphere32.json) at 1e-9.
+
+Stored results are written by tests/golden/make_oracle_fixtures.py from oracle/ only.
+"""
+import concurrent.futures as cf
+import hashlib
+import json
+import multiprocessing as mp
+import os
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from conftest import GOLDEN
+from oracle import em as om
+from paper_1504_07499_gb300 import hmg, inputs as I
+
+from test_gpu_parity import kerr
+
+K3 = I.K_PHASES
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_1504_07499_gb300 import build
+    build.build()
+    c = hmg.Context(0)
+    yield c
+    c.close()
+
+
+def _oracle_sweeps(args):
+    ph, k, j, n = args
+    E = np.zeros(3)
+    E[j] = 1.0
+    return om.em_solve(ph, k, E, tol=1e-8, max_iter=n).e
+
+
+def _stored(name):
+    with open(os.path.join(GOLDEN, f"oracle_{name}.json")) as fh:
+        return json.load(fh)
+
+
+def _phase(ctx, case):
+    p = case["params"]
+    spheres = I.centred_sphere(p["centred"]) if "centred" in p else I.generate_spheres(p["seed"], p["n"], p["f"]).spheres
+    ph = ctx.voxelize(spheres, p["layer"], p["N"])
+    assert hashlib.sha256(ph.tobytes()).hexdigest() == case["phase_sha256"]   # the oracle's grid
+    return ph
+
+
+@pytest.mark.parametrize("N", [192, 256])
+def test_benchmark_rve_eight_chained_sweeps_every_voxel(ctx, N):
+    sl = I.generate_spheres(3000, 100, 0.40)
+    ph = om.voxelize(sl.spheres, 0.3, N)
+    # the oracle's three gradients in parallel worker processes (spawned: this process
+    # already holds a CUDA context)
+    with cf.ProcessPoolExecutor(3, mp_context=mp.get_context("spawn")) as ex:
+        fut = [ex.submit(_oracle_sweeps, (ph, K3, j, 8)) for j in range(3)]
+        e = np.empty((3, 3, N, N, N))
+        K, info, st = hmg.hmg_solve_fields(ctx.handle, ph, N, K3, 1e-8, hmg.HMG_FP32_BULK, e, max_iter=8,
+                                           allow=(hmg.HMG_NOT_CONVERGED,))
+        ref = [f.result() for f in fut]
+    assert st == hmg.HMG_NOT_CONVERGED
+    assert list(info["iters"]) == [8, 8, 8] and list(info["iters_fp64"]) == [0, 0, 0]
+    assert (hmg.hmg_get_variant(ctx.handle, N) & 4) == 0          # chained sweeps ran
+    for j in range(3):
+        err = np.abs(e[j] - ref[j]).max() / np.abs(ref[j]).max()
+        assert err < 1e-5, (N, j, err)
+
+
+@pytest.mark.parametrize("prec,tol,iters_exact", [(hmg.HMG_FP32_BULK, 1e-5, False), (hmg.HMG_FP64, 1e-9, True)])
+def test_benchmark_rve_K_against_stored_oracle(ctx, prec, tol, iters_exact):
+    case = _stored("rsa256_s3000")
+    p = case["params"]
+    ph = _phase(ctx, case)
+    K, info, st = ctx.solve(ph, tuple(p["k"]), p["tol"], prec)
+    assert st == hmg.HMG_OK
+    assert kerr(K, np.array(case["K"])) < tol
+    assert all(e < p["tol"] for e in info["eps_eq"])
+    if iters_exact:
+        assert all(abs(a - b) <= 1 for a, b in zip(info["iters"], case["iters"]))
+
+
+@pytest.mark.parametrize("prec,tol,iters_exact", [(hmg.HMG_FP32_BULK, 1e-5, False), (hmg.HMG_FP64, 1e-9, True)])
+def test_contrast_2e4_K_against_stored_oracle(ctx, prec, tol, iters_exact):
+    case = _stored("rsa64_s3000_c2e4")
+    p = case["params"]
+    ph = _phase(ctx, case)
+    K, info, st = ctx.solve(ph, tuple(p["k"]), p["tol"], prec)
+    assert st == hmg.HMG_OK
+    assert kerr(K, np.array(case["K"])) < tol
+    if iters_exact:
+        assert all(abs(a - b) <= 1 for a, b in zip(info["iters"], case["iters"]))
+
+
+@pytest.mark.parametrize("prec,tol", [(hmg.HMG_FP64, 1e-9), (hmg.HMG_FP32_BULK, 1e-5)])
+def test_centred_sphere_32_is_isotropic_and_matches_oracle(ctx, prec, tol):
+    case = _stored("sphere32")
+    p = case["params"]
+    ph = _phase(ctx, case)
+    K, info, st = ctx.solve(ph, tuple(p["k"]), p["tol"], prec)
+    assert st == hmg.HMG_OK
+    Kref = np.array(case["K"])
+    assert kerr(K, Kref) < tol
+    kappa = np.trace(K) / 3.0
+    # cubic symmetry of the grid: equal diagonal entries (up to the stopping tolerance)
+    # and vanishing off-diagonals (rounding level in FP64, tolerance level in FP32 bulk)
+    assert np.abs(np.diag(K) - kappa).max() < 1e-8 * kappa
+    off = 1e-10 if prec == hmg.HMG_FP64 else 1e-8
+    assert np.abs(K - np.diag(np.diag(K))).max() < off * kappa
+    if prec == hmg.HMG_FP64:
+        assert all(abs(a - b) <= 1 for a, b in zip(info["iters"], case["iters"]))

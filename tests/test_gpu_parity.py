@@ -6,8 +6,9 @@ Tolerances:
 * FP32 transforms: 2e-6 relative to the largest coefficient (FP32 FFT error
   ~ eps32 * log2(N^3)); FP32 sweeps: 1e-5 relative.
 * Full solves: FP64 K within 1e-9 relative and the same sweep counts (+-1);
-  FP32-bulk K within 1e-5 per entry (relative to the diagonal scale of its row and
-  column) and the gradient field within 1e-4 relative L2.
+  FP32-bulk K within 1e-5 relative on each entry (entries below 1 % of the largest
+  diagonal entry relative to that 1 %, see ``kerr``) and the gradient field within
+  1e-4 relative L2.
 """
 import numpy as np
 import pytest
@@ -49,10 +50,16 @@ def unpack_spectrum(Z, N):
     return full
 
 
+KERR_FLOOR = 1e-2
+
+
 def kerr(K, Kref):
-    """Per-entry error scaled by sqrt(K_ii K_jj) of the reference."""
-    d = np.sqrt(np.abs(np.outer(np.diag(Kref), np.diag(Kref))))
-    return (np.abs(K - Kref) / d).max()
+    """Largest relative error over the entries of K.  Each entry is compared with
+    itself (|K_ij - Kref_ij| / |Kref_ij|) when it is at least KERR_FLOOR times the
+    largest diagonal entry; smaller entries (off-diagonals that vanish by symmetry or
+    nearly so) are compared with that floor instead."""
+    floor = KERR_FLOOR * np.abs(np.diag(Kref)).max()
+    return (np.abs(K - Kref) / np.maximum(np.abs(Kref), floor)).max()
 
 
 # --- voxelization (§2) -------------------------------------------------------------
