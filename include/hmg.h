@@ -266,8 +266,12 @@ hmg_status hmg_poll(hmg_ctx* ctx, uint64_t ticket, double K_out[9], hmg_info* in
  *          (0, the default: the x inverse of one sweep and the x forward of the next
  *          are one kernel and the field is stored only before the residual sweep) or
  *          not (1).  Chained and unchained sweeps give bit-identical results.
- * The autotuner chooses bits 0 and 1 and leaves bit 2 clear.  hmg_set_variant pins
- * `variant` (0 .. 7) for size N, or clears the choice (-1) so that the next solve
+ *   bit 3: with chained sweeps, the x round trip runs as one launch per CTA of each
+ *          row block (0) or as a persistent kernel (1) whose CTAs stage the spectrum
+ *          and phase rows of their next row block in shared memory with bulk copies
+ *          while they transform the current one (bit-identical results).
+ * The autotuner chooses bits 0, 1 and 3 and leaves bit 2 clear.  hmg_set_variant pins
+ * `variant` (0 .. 15) for size N, or clears the choice (-1) so that the next solve
  * times them again.  All give the same results to rounding. */
 hmg_status hmg_set_variant(hmg_ctx* ctx, int N, int variant);
 

@@ -238,8 +238,21 @@ int autotune_z(::hmg_ctx* c, GridDesc g, SolveState* s, cudaStream_t st) {
         }
         xybest = xyms[1] < xyms[0] ? 1 : 0;
     }
+    // chained x round trip: the plain kernel or the persistent one with staged rows
+    int xpbest = 0;
+    g.zvar = zbest;
+    g.xyvar = xybest;
+    if (chain_sweeps(g)) {
+        float xms[2];
+        for (int v = 0; v < 2; ++v) {
+            g.xpers = v;
+            xms[v] = time_launches(st, [&] { fast_x_round(g, false, false, all, s->spec32, s->f32buf, nullptr, st); }, 6);
+        }
+        xpbest = xms[1] < xms[0] ? 1 : 0;
+        if (fast_take_wait_failure()) xpbest = 0;
+    }
     cudaGetLastError();
-    best = zbest | (xybest << 1);
+    best = zbest | (xybest << 1) | (xpbest << 3);
     c->ztune[g.N] = best;
     return best;
 }
@@ -731,6 +744,10 @@ hmg_status Solver::run_bulk(int max_iter, double tol, hmg_info* info, double K[9
     }
     cudaEventDestroy(ready);
     if (err != HMG_OK) return err;
+    if (g.xpers && fast_take_wait_failure()) {
+        set_error("a persistent kernel gave up waiting for its bulk copies; results are invalid");
+        return HMG_CUDA_ERROR;
+    }
     unsigned left = 0;
     for (int sl = 0; sl < g.nslots; ++sl)
         if (status[sl] == HMG_NOT_CONVERGED) {

@@ -18,6 +18,9 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
+
+#include "hmg_async.cuh"
 #include "hmg_fft.cuh"
 #include "hmg_green.cuh"
 #include "hmg_internal.h"
@@ -598,6 +601,114 @@ k_fx_round(GridDesc g, unsigned mask, float2* __restrict__ spec, float* __restri
     row_forward_split<M, TP, E>(v, t, rs, twM, twN, sp);
 }
 
+// Set by a persistent kernel whose bounded wait for a bulk copy gave up (read and
+// cleared by fast_take_wait_failure).
+__device__ unsigned g_wait_fail;
+
+// Dynamic shared memory of k_fx_round_p: the staged spectrum rows of one block (each
+// row padded by 64 bytes, so that the two rows a half-warp reads fall on different bank
+// halves), the block's phase rows, and the rows' exchange buffers.
+template <int M, int RW>
+struct RoundSmem {
+    static constexpr int SROW = M + 8;
+    static constexpr size_t spec_bytes = (size_t)RW * SROW * sizeof(float2);
+    static constexpr size_t phase_off = spec_bytes;
+    static constexpr size_t phase_bytes = (size_t)RW * 2 * M;
+    static constexpr size_t x_off = (phase_off + phase_bytes + 15) / 16 * 16;
+    static constexpr size_t total = x_off + (size_t)RW * row_stride<M>() * sizeof(float2);
+};
+
+// k_fx_round as a persistent kernel: each CTA walks row blocks (slot, component, rows)
+// in a fixed stride over the grid.  While the rows of one block are transformed, the
+// bulk-copy engine stages the spectrum and phase rows of the CTA's next block in shared
+// memory, so the HBM reads of a block overlap the arithmetic of the one before (the plain
+// kernel exposes the load latency of its single block).  The defect r is loaded from
+// global memory at the start of a block and is in flight during the inverse transform.
+// Same float operations as k_fx_round, so results are identical.
+template <int M, int RW, bool ADDR, bool WTAU>
+__global__ void __launch_bounds__(RW * Split<M>::TP, 512 / (RW * Split<M>::TP))
+k_fx_round_p(GridDesc g, unsigned mask, float2* __restrict__ spec, float* __restrict__ tau,
+             const float* __restrict__ r32, int nblk) {
+    constexpr int E = Split<M>::E, TP = Split<M>::TP, RS = row_stride<M>();
+    using L = RoundSmem<M, RW>;
+    constexpr int N = 2 * M;
+    extern __shared__ __align__(128) unsigned char dsm[];
+    float2* sspec = reinterpret_cast<float2*>(dsm);
+    unsigned char* sphase = dsm + L::phase_off;
+    __shared__ float2 lut[16];
+    __shared__ float2 tws[2 * M];
+    __shared__ __align__(8) unsigned long long mbar;
+    __shared__ int s_ok;
+    const int t = threadIdx.x % TP, r = threadIdx.x / TP;
+    const int nitems = g.nslots * nblk;
+    int item = blockIdx.x;
+    while (item < nitems && !slot_active(g, mask, item / nblk)) item += gridDim.x;
+    if (item >= nitems) return;
+    const uint32_t mb = async::smem_addr(&mbar);
+    if (threadIdx.x == 0) async::mbar_init(mb);
+    coef_pairs(lut, (float)g.Y[0], (float)g.Y[1], (float)g.Y[2]);
+    stage_twiddles<M>(tws, g);
+    // thread 0: stage the spectrum rows and phase rows of block `it`
+    auto issue = [&](int it) {
+        const int slot = it / nblk, b = it % nblk;
+        const long long row0 = (b % 3) * g.NN + (long long)(b / 3) * RW;
+        const float2* src = spec + (long long)slot * 3 * g.NNM + row0 * M;
+        async::mbar_expect(mb, (uint32_t)(RW * M * sizeof(float2) + RW * N));
+        for (int rr = 0; rr < RW; ++rr)
+            async::bulk_g2s(async::smem_addr(sspec + rr * L::SROW), src + (long long)rr * M, M * sizeof(float2), mb);
+        async::bulk_g2s(async::smem_addr(sphase), g.phase + (long long)(b / 3) * RW * N, RW * N, mb);
+    };
+    if (threadIdx.x == 0) issue(item);
+    __syncthreads();   // barrier initialized, tables staged
+    const float2* twM = tws;
+    const float2* twN = tws + M;
+    float2* rs = reinterpret_cast<float2*>(dsm + L::x_off) + r * RS;
+    uint32_t parity = 0;
+    while (item < nitems) {
+        const int slot = item / nblk, b = item % nblk;
+        const long long row = (b % 3) * g.NN + (long long)(b / 3) * RW + r;   // c*NN + z*N + y
+        const long long fbase = (long long)slot * 3 * g.N3 + row * N;
+        const bool addr = ADDR && (g.dflags ? (g.dflags[slot] & SF_ADDR) != 0 : true);
+        float2 radd[E];
+        if (addr) s2_load<M>(radd, reinterpret_cast<const float2*>(r32 + fbase), t);
+        // this block's copies: one thread decides for the CTA whether the wait succeeded
+        if (threadIdx.x == 0) s_ok = async::mbar_wait(mb, parity) ? 1 : 0;
+        __syncthreads();
+        if (!s_ok) {
+            if (threadIdx.x == 0) atomicOr(&g_wait_fail, 1u);
+            return;
+        }
+        async::mbar_wait(mb, parity);   // complete already: the copied bytes are visible here
+        parity ^= 1u;
+        float2 xk[E];
+#pragma unroll
+        for (int n1 = 0; n1 < E; ++n1) xk[n1] = sspec[r * L::SROW + TP * n1 + t];
+        uchar2 q[E];
+        s2_load_phase<M>(q, reinterpret_cast<const uchar2*>(sphase + r * N), t);
+        __syncthreads();   // every thread holds its rows: the buffers take the next block
+        int nxt = item + gridDim.x;
+        while (nxt < nitems && !slot_active(g, mask, nxt / nblk)) nxt += gridDim.x;
+        if (threadIdx.x == 0 && nxt < nitems) issue(nxt);
+        // x inverse (steps 5), update (step 7), optional store, polarization (step 2)
+        float2 v[E];
+        c2r_merge_shfl<M, TP, E>(v, xk, twN, t);
+        stage1_write<M, false, true>(v, t, twM, rs, 1);
+        __syncthreads();
+        stage2_read<M, false>(v, t, rs, 1);
+#pragma unroll
+        for (int j = 0; j < E; ++j)
+            if (addr) v[j] = make_float2(__fadd_rn(v[j].x, radd[j].x), __fadd_rn(v[j].y, radd[j].y));
+        if (WTAU) s2_store<M>(reinterpret_cast<float2*>(tau + fbase), v, t);
+#pragma unroll
+        for (int j = 0; j < E; ++j) v[j] = __fmul2_rn(v[j], lut[pair_index(q[j])]);
+        __syncthreads();   // every thread has read its stage-2 values from rs
+        // forward transform (step 3) and real split, written over the rows it came from
+        row_forward_split<M, TP, E>(v, t, rs, twM, twN, spec + (long long)slot * 3 * g.NNM + row * M);
+        __syncthreads();   // rs and s_ok are reused by the next block
+        item = nxt;
+    }
+}
+
 }  // namespace fast
 
 // ---------------------------------------------------------------------------
@@ -796,10 +907,70 @@ bool chain_sweeps(const GridDesc& g) {
     return !g.nochain && !(g.xyvar == 1 && fused_cluster(g.N)) && fast_x_ctas(g) > 0;
 }
 
+namespace {
+// Grid of a persistent kernel: as many CTAs as fit on the GPU at once (occupancy of the
+// kernel at its shared memory), at most one per work item.
+template <typename K>
+int persistent_grid(K kern, int threads, size_t smem, int items) {
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    }
+    if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int per = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, threads, smem) != cudaSuccess || per < 1) per = 1;
+    return std::max(1, std::min(items, per * std::max(sms, 1)));
+}
+template <int M, bool ADDR, bool WTAU>
+void launch_round_p(const GridDesc& g, unsigned mask, float2* sp, float* tau, const float* r32, cudaStream_t st) {
+    constexpr int RW = fx_rows<M>();
+    constexpr int T = RW * fast::Split<M>::TP;
+    constexpr size_t sm = fast::RoundSmem<M, RW>::total;
+    auto kern = fast::k_fx_round_p<M, RW, ADDR, WTAU>;
+    const int nblk = fast_x_ctas(g);
+    const int grid = persistent_grid(kern, T, sm, nblk * g.nslots);
+    kern<<<grid, T, sm, st>>>(g, mask, sp, tau, r32, nblk);
+}
+}  // namespace
+
+bool fast_take_wait_failure() {
+    unsigned v = 0;
+    if (cudaMemcpyFromSymbol(&v, fast::g_wait_fail, sizeof v) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    if (v) {
+        const unsigned z = 0;
+        cudaMemcpyToSymbol(fast::g_wait_fail, &z, sizeof z);
+    }
+    return v != 0;
+}
+
 bool fast_x_round(const GridDesc& g, bool addr, bool wtau, unsigned mask, void* spec, float* tau, const float* r32,
                   cudaStream_t st) {
     float2* sp = reinterpret_cast<float2*>(spec);
     if (!fast_x_ctas(g)) return false;
+    if (g.xpers) {
+#define FXRP(M)                                                                            \
+    {                                                                                      \
+        if (addr && wtau) launch_round_p<M, true, true>(g, mask, sp, tau, r32, st);        \
+        else if (addr) launch_round_p<M, true, false>(g, mask, sp, tau, r32, st);          \
+        else if (wtau) launch_round_p<M, false, true>(g, mask, sp, tau, r32, st);          \
+        else launch_round_p<M, false, false>(g, mask, sp, tau, r32, st);                   \
+    }
+        switch (g.M) {
+            HMG_FAST_LEN(32, FXRP)
+            HMG_FAST_LEN(48, FXRP)
+            HMG_FAST_LEN(64, FXRP)
+            HMG_FAST_LEN(96, FXRP)
+            HMG_FAST_LEN(128, FXRP)
+            HMG_FAST_LEN(256, FXRP)
+            default: return false;
+        }
+#undef FXRP
+    }
 #define FXR(M)                                                                                                      \
     {                                                                                                               \
         constexpr int RW = fx_rows<M>();                                                                            \

@@ -46,6 +46,8 @@ struct GridDesc {
     int zvar;              // z-pass kernel variant of the register-resident path (autotuned)
     int xyvar;             // 1: fused x + y cluster kernels, 0: separate x and y passes (autotuned)
     int nochain;           // 1: FP32 sweeps of a block are not chained through k_fx_round
+    int xpers;             // 1: the chained x round trip runs as a persistent kernel that
+                           //    stages its next rows with bulk copies (autotuned)
     // Per-slot flags in device memory (engine launches; nullptr = use the launch's
     // mask and template modes): SF_ACTIVE, SF_ADDB (add gc E at DC, plain sweep),
     // SF_ADDR (add the defect r, correction sweep).  `resid`: this launch of the x
@@ -111,6 +113,9 @@ bool fast_x_round(const GridDesc& g, bool addr, bool wtau, unsigned mask, void* 
 // FP32 sweeps of a block are chained (x inverse + next x forward in one kernel):
 // register-resident x kernels exist for g.N, separate x and y passes, chaining not off.
 bool chain_sweeps(const GridDesc& g);
+// True (and cleared) when a persistent kernel's bounded wait for a bulk copy gave up
+// since the last call; the results of that launch are invalid.
+bool fast_take_wait_failure();
 int fast_x_ctas(const GridDesc& g);
 int fast_z_ctas(const GridDesc& g);
 
