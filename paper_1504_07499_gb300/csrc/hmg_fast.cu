@@ -935,6 +935,20 @@ void launch_round_p(const GridDesc& g, unsigned mask, float2* sp, float* tau, co
 }
 }  // namespace
 
+namespace {
+int fast_split_e(int M) {
+    switch (M) {
+        case 32: return fast::Split<32>::E;
+        case 48: return fast::Split<48>::E;
+        case 64: return fast::Split<64>::E;
+        case 96: return fast::Split<96>::E;
+        case 128: return fast::Split<128>::E;
+        case 256: return fast::Split<256>::E;
+        default: return 0;
+    }
+}
+}  // namespace
+
 bool fast_take_wait_failure() {
     unsigned v = 0;
     if (cudaMemcpyFromSymbol(&v, fast::g_wait_fail, sizeof v) != cudaSuccess) {
@@ -952,7 +966,9 @@ bool fast_x_round(const GridDesc& g, bool addr, bool wtau, unsigned mask, void* 
                   cudaStream_t st) {
     float2* sp = reinterpret_cast<float2*>(spec);
     if (!fast_x_ctas(g)) return false;
-    if (g.xpers) {
+    // the persistent form of the correction sweeps (r added) of 24-value rows would keep
+    // r in registers beside the transform and spill; those use the plain kernel
+    if (g.xpers && !(addr && fast_split_e(g.M) > 16)) {
 #define FXRP(M)                                                                            \
     {                                                                                      \
         if (addr && wtau) launch_round_p<M, true, true>(g, mask, sp, tau, r32, st);        \

@@ -156,3 +156,25 @@ def test_chained_engine_batch_is_bit_identical(ctx):
     assert np.array_equal(res[0][0], res[1][0])
     for a, b in zip(res[0][1], res[1][1]):
         assert list(a["iters"]) == list(b["iters"])
+
+
+@pytest.mark.parametrize("N", [64, 96, 128])
+def test_persistent_x_round_is_bit_identical(ctx, N):
+    """Chained sweeps with the persistent x round trip (variant bit 3: bulk copies stage
+    the next row block) against the plain kernel: the same K, sweep counts and fields,
+    bit for bit, correction sweeps (r added) included."""
+    sl = I.generate_spheres(1000, 30, 0.2)
+    ph = om.voxelize(sl.spheres, 0.3, N)
+    k = (0.20, 0.25, 40.0)
+    out = []
+    for v in (0, 8):
+        hmg.hmg_set_variant(ctx.handle, N, v)
+        e = np.empty((3, 3, N, N, N))
+        K, info, st = hmg.hmg_solve_fields(ctx.handle, ph, N, k, 1e-8, hmg.HMG_FP32_BULK, e)
+        assert st == hmg.HMG_OK
+        assert info["fp64_rounds"] > 0          # correction sweeps ran
+        out.append((K, info, e))
+    hmg.hmg_set_variant(ctx.handle, N, -1)
+    assert np.array_equal(out[0][0], out[1][0])
+    assert list(out[0][1]["iters"]) == list(out[1][1]["iters"])
+    assert np.array_equal(out[0][2], out[1][2])
