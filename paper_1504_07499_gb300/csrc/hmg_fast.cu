@@ -405,6 +405,14 @@ __device__ __forceinline__ void r2c_split_shfl(const float2* v, int t, const flo
     }
 }
 
+// A row's TP threads are TP consecutive lanes of one warp and its exchange buffer is its
+// own, so the exchanges of an x row transform synchronize the warp, not the CTA.
+template <int TP>
+__device__ __forceinline__ void row_sync() {
+    static_assert(TP <= 32 && 32 % TP == 0, "a row's threads must lie in one warp");
+    __syncwarp();
+}
+
 // Forward x transform of a row held in the stage-2 layout, ending with the real split
 // written to dst: decimation-in-frequency stages (one shared-memory exchange), the split
 // with the partner values exchanged by warp shuffles.  Ends without a barrier.
@@ -412,7 +420,7 @@ template <int M, int TP, int E>
 __device__ __forceinline__ void row_forward_split(float2* v, int t, float2* rs, const float2* __restrict__ twM,
                                                   const float2* __restrict__ twN, float2* __restrict__ dst) {
     rstage2_write<M, true, true>(v, t, twM, rs, 1);
-    __syncthreads();
+    row_sync<TP>();
     rstage1_read<M, true>(v, t, rs, 1);   // v[kb] = Z[t + TP kb]
     r2c_split_shfl<M, TP, E>(v, t, twN, dst);
 }
@@ -497,7 +505,7 @@ __device__ __forceinline__ void row_inverse(float2* v, int t, float2* rs, const 
     for (int n1 = 0; n1 < E; ++n1) xk[n1] = src[TP * n1 + t];
     c2r_merge_shfl<M, TP, E>(v, xk, twN, t);
     stage1_write<M, false, true>(v, t, twM, rs, 1);
-    __syncthreads();
+    row_sync<TP>();
     stage2_read<M, false>(v, t, rs, 1);
 }
 
@@ -596,7 +604,7 @@ k_fx_round(GridDesc g, unsigned mask, float2* __restrict__ spec, float* __restri
     if (WTAU) s2_store<M>(reinterpret_cast<float2*>(tau + fbase), v, t);
 #pragma unroll
     for (int j = 0; j < E; ++j) v[j] = __fmul2_rn(v[j], lut[pair_index(q[j])]);
-    __syncthreads();   // every thread has read its stage-2 values from rs
+    row_sync<TP>();   // the row's threads have read their stage-2 values from rs
     // forward transform and real split, written over the row it came from
     row_forward_split<M, TP, E>(v, t, rs, twM, twN, sp);
 }
@@ -693,7 +701,7 @@ k_fx_round_p(GridDesc g, unsigned mask, float2* __restrict__ spec, float* __rest
         float2 v[E];
         c2r_merge_shfl<M, TP, E>(v, xk, twN, t);
         stage1_write<M, false, true>(v, t, twM, rs, 1);
-        __syncthreads();
+        row_sync<TP>();
         stage2_read<M, false>(v, t, rs, 1);
 #pragma unroll
         for (int j = 0; j < E; ++j)
@@ -701,10 +709,11 @@ k_fx_round_p(GridDesc g, unsigned mask, float2* __restrict__ spec, float* __rest
         if (WTAU) s2_store<M>(reinterpret_cast<float2*>(tau + fbase), v, t);
 #pragma unroll
         for (int j = 0; j < E; ++j) v[j] = __fmul2_rn(v[j], lut[pair_index(q[j])]);
-        __syncthreads();   // every thread has read its stage-2 values from rs
+        row_sync<TP>();   // the row's threads have read their stage-2 values from rs
         // forward transform (step 3) and real split, written over the rows it came from
         row_forward_split<M, TP, E>(v, t, rs, twM, twN, spec + (long long)slot * 3 * g.NNM + row * M);
-        __syncthreads();   // rs and s_ok are reused by the next block
+        row_sync<TP>();   // rs is reused by the next block (s_ok and the staging buffers are
+                          // next written after CTA barriers every thread has passed)
         item = nxt;
     }
 }
