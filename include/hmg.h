@@ -77,9 +77,22 @@ typedef enum { HMG_FP64 = 0, HMG_FP32_BULK = 1 } hmg_precision;
  *     (P = xi xi^T / |xi|^2); contraction (c - 1)/(c + 1) per sweep.  Steps 1 and 6
  *     (the two convergence tests) are those of the §3 Algorithm; its new iterate is the
  *     compatible field of step 5.
- * Both converge to the same discrete solution (the fixed point of either is the
+ *   HMG_SCHEME_AUGMENTED_LAGRANGIAN: the augmented Lagrangian scheme (Michel, Moulinec
+ *     & Suquet 2001, cited in §5 for the choice of k0): alternate minimization of the
+ *     Lagrangian <d.k d>/2 + <lambda.(e - d)> + k0 <|e - d|^2>/2 over a compatible field e
+ *     (mean grad Theta) and a free field d, then the multiplier update
+ *     lambda += k0 (e - d), with k0 = sqrt(min k * max k).  Its iterate d (and flux
+ *     lambda = k d) moves half the Eyre-Milton step: step 7 with the factor 1 in place
+ *     of 2, contraction (1 + rho)/2 per sweep with rho = (sqrt c - 1)/(sqrt c + 1), so it
+ *     needs about twice the sweeps but also converges when rho -> 1 (infinite contrast).
+ *     Steps 1 and 6 test its iterate d (eps_comp = |d - e|, eps_eq on lambda = k d).
+ * All converge to the same discrete solution (the fixed point of each is the
  * compatible field with divergence-free flux), so K agrees to the tolerance. */
-typedef enum { HMG_SCHEME_EYRE_MILTON = 0, HMG_SCHEME_BASIC = 1 } hmg_scheme;
+typedef enum {
+    HMG_SCHEME_EYRE_MILTON = 0,
+    HMG_SCHEME_BASIC = 1,
+    HMG_SCHEME_AUGMENTED_LAGRANGIAN = 2
+} hmg_scheme;
 
 /* Per-solve report.  Index j is the macroscopic gradient e_j. */
 typedef struct {
@@ -148,11 +161,26 @@ hmg_status hmg_solve_fields(hmg_ctx* ctx, const uint8_t* phase, int N, double k_
  * The basic scheme needs about ln(1/tol) (c + 1) / 2 sweeps per gradient at contrast c
  * (18 500 at c = 2000, tol 1e-8): raise max_iter above its default of 20000 for
  * contrasts beyond ~2000.
+ * The augmented Lagrangian scheme needs about twice the sweeps of the accelerated one.
  * Errors: HMG_INVALID_ARG for an unknown scheme, otherwise as hmg_solve. */
 hmg_status hmg_solve_scheme(hmg_ctx* ctx, const uint8_t* phase, int N, double k_matrix,
                             double k_incl, double k_coat, double tol,
                             hmg_precision precision, hmg_scheme scheme, int max_iter,
                             double K_out[9], hmg_info* info, double* e_out);
+
+/* The polarization scheme named in §3 (beside the basic, dual, augmented Lagrangian and
+ * accelerated schemes; the paper prints no formula).  Read here as the relaxed
+ * iteration on the polarization tau = (k + k0) e with relaxation beta,
+ *   tau^{n+1} = (1 - beta/2) tau^n + (beta/2) [(I - 2P)(Y tau^n) + 2 k0 E],
+ * i.e. step 7 of the §3 Algorithm with the factor beta in place of 2:
+ * e^{n+1} = e^n + beta k0 / (k + k0) (e_comp - e^n).  beta = 2 is the accelerated
+ * (Eyre-Milton) scheme, beta = 1 the augmented Lagrangian scheme; every beta in (0, 2]
+ * has the same fixed point and contracts by 1 - beta (1 - rho) / 2 per sweep.
+ * Errors: HMG_INVALID_ARG for beta outside (0, 2], otherwise as hmg_solve_scheme. */
+hmg_status hmg_solve_polarization(hmg_ctx* ctx, const uint8_t* phase, int N, double k_matrix,
+                                  double k_incl, double k_coat, double tol,
+                                  hmg_precision precision, double beta, int max_iter,
+                                  double K_out[9], hmg_info* info, double* e_out);
 
 /* Run `n_iter` sweeps of steps 2-7 of §3 (no convergence test) on a given gradient
  * field, for one macroscopic gradient grad_Theta (3 doubles, host).

@@ -17,7 +17,9 @@ Everything here is plain FP64 numpy written from the paper:
 * §3, Algorithm, steps 1-7, in the paper's order and notation (gradient form e = grad theta).
 * §3 last paragraph: <phi> = -L_hom grad Theta gives the effective tensor.
 * §3 (the list of FFT-based schemes) and eqs. 1-3: the basic scheme, the plain
-  fixed-point iteration of the Lippmann-Schwinger equation (``basic_solve``).
+  fixed-point iteration of the Lippmann-Schwinger equation (``basic_solve``), the
+  augmented Lagrangian scheme from its Lagrangian (``al_solve``), and the polarization
+  scheme read as step 7 with a relaxation beta in place of 2 (``em_solve(beta=...)``).
 
 The 3D DFT is the direct sum (``dft3_direct``, taken axis by axis) on grids up to
 16^3, and the library FFT (scipy.fft) above that, which the tests pin against the
@@ -279,9 +281,13 @@ def compatibility_residual(e: np.ndarray, ec: np.ndarray, normE: float) -> float
 
 
 def em_solve(phase: np.ndarray, k_phases, grad_Theta, tol: float = 1e-8,
-             max_iter: int = 20000, record: bool = False, e0: np.ndarray | None = None) -> EMResult:
+             max_iter: int = 20000, record: bool = False, e0: np.ndarray | None = None,
+             beta: float = 2.0) -> EMResult:
     """Eyre-Milton accelerated scheme of §3 (Algorithm, steps 1-7) for one macroscopic
-    gradient grad_Theta, in the gradient form and the paper's notation."""
+    gradient grad_Theta, in the gradient form and the paper's notation.
+
+    ``beta`` replaces the factor 2 of step 7 (the polarization family read for the
+    polarization scheme §3 names: 2 is the accelerated scheme itself)."""
     N = phase.shape[0]
     k_field = np.asarray(k_phases, dtype=np.float64)[phase]
     L0 = -reference_k0(k_phases)                 # L0 = -sqrt(min * max) I   (§5)
@@ -316,13 +322,14 @@ def em_solve(phase: np.ndarray, k_phases, grad_Theta, tol: float = 1e-8,
             hist_c.append(eps_comp)
         if not math.isfinite(eps_comp):
             break
-        # Step 7: e^{n+1} = e^n - 2 (L - L0)^{-1} L0 (e_comp - e^n).
-        e = e - 2.0 * (L0 / (k_field - L0))[None] * (ec - e)
+        # Step 7: e^{n+1} = e^n - 2 (L - L0)^{-1} L0 (e_comp - e^n)  (beta in place of 2).
+        e = e - beta * (L0 / (k_field - L0))[None] * (ec - e)
     eps_eq, mean_phi = equilibrium_residual(k_field, e, xi)
     return EMResult(e, mean_phi, max_iter, False, eps_eq, hist_c, hist_q)
 
 
-def effective_tensor(phase: np.ndarray, k_phases, tol: float = 1e-8, max_iter: int = 20000):
+def effective_tensor(phase: np.ndarray, k_phases, tol: float = 1e-8, max_iter: int = 20000,
+                     beta: float = 2.0):
     """L_hom from <phi> = -L_hom grad Theta for the three unit gradients (§3).
     Returns (K (3x3, column j answers gradient e_j), [EMResult] * 3)."""
     K = np.zeros((3, 3))
@@ -330,7 +337,77 @@ def effective_tensor(phase: np.ndarray, k_phases, tol: float = 1e-8, max_iter: i
     for j in range(3):
         E = np.zeros(3)
         E[j] = 1.0
-        r = em_solve(phase, k_phases, E, tol, max_iter)
+        r = em_solve(phase, k_phases, E, tol, max_iter, beta=beta)
+        K[:, j] = -r.flux_mean
+        res.append(r)
+    return K, res
+
+
+# ---------------------------------------------------------------------------
+# §3 augmented Lagrangian scheme (named in §3's list of FFT-based schemes; the
+# paper prints no formula).  Written from its definition in Michel, Moulinec &
+# Suquet (2001), cited in §5: the cell problem is the minimization of <e.k e>/2
+# over compatible fields e with mean grad Theta; a free field d with the constraint
+# d = e and a multiplier lambda give the augmented Lagrangian
+#     <d.k d>/2 + <lambda.(e - d)> + k0 <|e - d|^2>/2,
+# minimized alternately over e (compatible: a Fourier projection) and d (pointwise),
+# followed by the multiplier step.  Reading: penalty k0 = sqrt(min k * max k) as for
+# the accelerated scheme (§5); the two tests of the §3 Algorithm are applied to the
+# iterate d (step 6: |d - e| of the compatible field e it gives; step 1: equilibrium
+# of the flux lambda).
+# ---------------------------------------------------------------------------
+
+
+def al_solve(phase: np.ndarray, k_phases, grad_Theta, tol: float = 1e-8,
+             max_iter: int = 40000, record: bool = False) -> EMResult:
+    """Augmented Lagrangian scheme for one macroscopic gradient.  EMResult.e is the
+    final iterate d; its flux is lambda."""
+    N = phase.shape[0]
+    k_field = np.asarray(k_phases, dtype=np.float64)[phase]
+    k0 = reference_k0(k_phases)
+    xi = wavevectors(N)
+    E = np.asarray(grad_Theta, dtype=np.float64)
+    normE = float(np.linalg.norm(E))
+    d = np.broadcast_to(E[:, None, None, None], (3, N, N, N)).copy()
+    lam = k_field[None] * d                        # multiplier: the flux of d
+    eps_comp = math.inf
+    hist_c, hist_q = [], []
+    eps_eq = math.inf
+    for n in range(max_iter):
+        # Step 1 on the current iterate: equilibrium of its flux
+        if eps_comp < tol:
+            eps_eq, mean_phi = equilibrium_residual(k_field, d, xi)
+            hist_q.append(eps_eq)
+            if eps_eq < tol:
+                return EMResult(d, mean_phi, n, True, eps_eq, hist_c, hist_q)
+        # e: minimize <lambda.e> + k0 <|e - d|^2>/2 over e = grad Theta + compatible
+        # fluctuation: e = grad Theta + P(d - lambda / k0), P = k0 Gamma0 for L0 = k0
+        q_hat = fft3(d - lam / k0)
+        e_hat = gamma0_apply(xi, k0, q_hat) * k0
+        e_hat[:, 0, 0, 0] = E * N ** 3
+        e = (ifft3_unnorm(e_hat) / N ** 3).real
+        # step 6 on the iterate d
+        eps_comp = compatibility_residual(d, e, normE)
+        if record:
+            hist_c.append(eps_comp)
+        if not math.isfinite(eps_comp):
+            break
+        # d: minimize <d.k d>/2 - <lambda.d> + k0 <|e - d|^2>/2 pointwise
+        d = (lam + k0 * e) / (k_field + k0)[None]
+        # multiplier step
+        lam = lam + k0 * (e - d)
+    eps_eq, mean_phi = equilibrium_residual(k_field, d, xi)
+    return EMResult(d, mean_phi, max_iter, False, eps_eq, hist_c, hist_q)
+
+
+def al_effective_tensor(phase: np.ndarray, k_phases, tol: float = 1e-8, max_iter: int = 40000):
+    """L_hom of the augmented Lagrangian scheme for the three unit gradients."""
+    K = np.zeros((3, 3))
+    res = []
+    for j in range(3):
+        E = np.zeros(3)
+        E[j] = 1.0
+        r = al_solve(phase, k_phases, E, tol, max_iter)
         K[:, j] = -r.flux_mean
         res.append(r)
     return K, res

@@ -118,7 +118,7 @@ std::shared_ptr<hmg::GridPlan> hmg_ctx::plan(int N) {
 namespace hmg {
 
 GridDesc make_desc(const GridPlan& gp, bool fp64, const double k[3], const uint8_t* phase_d,
-                   int nslots, int scheme) {
+                   int nslots, int scheme, double beta) {
     GridDesc g;
     memset(&g, 0, sizeof(g));
     const int N = gp.N, M = N / 2;
@@ -149,7 +149,12 @@ GridDesc make_desc(const GridPlan& gp, bool fp64, const double k[3], const uint8
         g.gc = 1.0;
         g.epsf = 1.0;
     } else {
-        // Eyre-Milton (tau = (k + k0) e): tau^{n+1} = (I - 2P)(Y tau^n) + 2 k0 E
+        // Eyre-Milton (tau = (k + k0) e): tau^{n+1} = (I - 2P)(Y tau^n) + 2 k0 E.  The
+        // augmented Lagrangian scheme (beta = 1) and the relaxed polarization iteration
+        // keep a fraction of the old field: tau^{n+1} = (1 - beta/2) tau^n + (beta/2) T tau^n,
+        // whose step moves beta/2 of the Eyre-Milton step, so the step-6 residual
+        // |e^n - e_comp^n| = |T tau^n - tau^n| / (2 k0) is |tau^{n+1} - tau^n| / (beta k0).
+        if (scheme == HMG_SCHEME_AUGMENTED_LAGRANGIAN) beta = 1.0;
         const double k0 = std::sqrt(kmin * kmax);
         g.k0 = k0;
         for (int p = 0; p < 3; ++p) {
@@ -160,7 +165,8 @@ GridDesc make_desc(const GridPlan& gp, bool fp64, const double k[3], const uint8
         g.ga = 1.0;
         g.gb = 2.0;
         g.gc = 2.0 * k0;
-        g.epsf = 1.0 / (2.0 * k0);
+        g.relax = 1.0 - 0.5 * beta;
+        g.epsf = 1.0 / (beta * k0);
     }
     for (int s = 0; s < kMaxSlots; ++s)
         for (int c = 0; c < 3; ++c) g.E[s][c] = (s == c) ? 1.0 : 0.0;

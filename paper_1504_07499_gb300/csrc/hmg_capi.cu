@@ -52,7 +52,7 @@ hmg_status check_common(hmg_ctx* ctx, int N, const void* p) {
 
 // Bring the phase grid onto the device and build the solve descriptor.
 hmg_status prepare(hmg_ctx* ctx, const uint8_t* phase, int N, const double k[3], bool fp64, int nslots,
-                   GridDesc* g, int scheme = HMG_SCHEME_EYRE_MILTON) {
+                   GridDesc* g, int scheme = HMG_SCHEME_EYRE_MILTON, double beta = 2.0) {
     auto gp = ctx->plan(N);
     if (!gp) {
         set_error("cannot allocate FFT tables");
@@ -66,13 +66,18 @@ hmg_status prepare(hmg_ctx* ctx, const uint8_t* phase, int N, const double k[3],
     const size_t N3 = (size_t)N * N * N;
     hmg_status st = cuda_status(copy_in(ctx->solve.phase, phase, N3, ctx->stream), "phase copy");
     if (st != HMG_OK) return st;
-    *g = make_desc(*gp, fp64, k, ctx->solve.phase, nslots, scheme);
+    *g = make_desc(*gp, fp64, k, ctx->solve.phase, nslots, scheme, beta);
     if (!fp64) {
         const int v = autotune_z(ctx, *g, &ctx->solve, ctx->stream);
         g->zvar = v & 1;
         g->xyvar = (v >> 1) & 1;
         g->nochain = (v >> 2) & 1;
         g->xpers = (v >> 3) & 1;
+    }
+    if (g->relax != 0.0) {   // relaxed schemes read the old field in every x inverse
+        g->xyvar = 0;
+        g->nochain = 1;
+        g->xpers = 0;
     }
     return HMG_OK;
 }
@@ -278,9 +283,10 @@ hmg_status hmg_voxelize(hmg_ctx* ctx, const hmg_sphere* spheres, size_t n, doubl
     return st;
 }
 
-hmg_status hmg_solve_scheme(hmg_ctx* ctx, const uint8_t* phase, int N, double km, double ki, double kc,
-                            double tol, hmg_precision precision, hmg_scheme scheme, int max_iter, double K_out[9],
-                            hmg_info* info, double* e_out) {
+namespace {
+hmg_status solve_impl(hmg_ctx* ctx, const uint8_t* phase, int N, double km, double ki, double kc, double tol,
+                      hmg_precision precision, int scheme, double beta, int max_iter, double K_out[9],
+                      hmg_info* info, double* e_out) {
     g_last_error.clear();
     auto t0 = std::chrono::steady_clock::now();
     hmg_status st = check_common(ctx, N, phase);
@@ -289,8 +295,13 @@ hmg_status hmg_solve_scheme(hmg_ctx* ctx, const uint8_t* phase, int N, double km
         set_error("bad K_out, conductivity, tolerance or precision");
         return HMG_INVALID_ARG;
     }
-    if (scheme != HMG_SCHEME_EYRE_MILTON && scheme != HMG_SCHEME_BASIC) {
-        set_error("unknown scheme %d", (int)scheme);
+    if (scheme != HMG_SCHEME_EYRE_MILTON && scheme != HMG_SCHEME_BASIC &&
+        scheme != HMG_SCHEME_AUGMENTED_LAGRANGIAN) {
+        set_error("unknown scheme %d", scheme);
+        return HMG_INVALID_ARG;
+    }
+    if (!(beta > 0.0 && beta <= 2.0)) {
+        set_error("relaxation beta = %g outside (0, 2]", beta);
         return HMG_INVALID_ARG;
     }
     if (max_iter <= 0) max_iter = 20000;
@@ -298,7 +309,7 @@ hmg_status hmg_solve_scheme(hmg_ctx* ctx, const uint8_t* phase, int N, double km
     const double k[3] = {km, ki, kc};
     const bool fp64 = precision == HMG_FP64;
     GridDesc g;
-    st = prepare(ctx, phase, N, k, fp64, 3, &g, (int)scheme);
+    st = prepare(ctx, phase, N, k, fp64, 3, &g, scheme, beta);
     if (st != HMG_OK) return st;
     Solver sv{g, &ctx->solve, ctx->stream, ctx->tracer.on ? &ctx->tracer : nullptr};
     hmg_info local;
@@ -319,6 +330,20 @@ hmg_status hmg_solve_scheme(hmg_ctx* ctx, const uint8_t* phase, int N, double km
     local.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     if (info) *info = local;
     return rs;
+}
+}  // namespace
+
+hmg_status hmg_solve_scheme(hmg_ctx* ctx, const uint8_t* phase, int N, double km, double ki, double kc,
+                            double tol, hmg_precision precision, hmg_scheme scheme, int max_iter, double K_out[9],
+                            hmg_info* info, double* e_out) {
+    return solve_impl(ctx, phase, N, km, ki, kc, tol, precision, (int)scheme, 2.0, max_iter, K_out, info, e_out);
+}
+
+hmg_status hmg_solve_polarization(hmg_ctx* ctx, const uint8_t* phase, int N, double km, double ki, double kc,
+                                  double tol, hmg_precision precision, double beta, int max_iter, double K_out[9],
+                                  hmg_info* info, double* e_out) {
+    return solve_impl(ctx, phase, N, km, ki, kc, tol, precision, HMG_SCHEME_EYRE_MILTON, beta, max_iter, K_out,
+                      info, e_out);
 }
 
 hmg_status hmg_solve_fields(hmg_ctx* ctx, const uint8_t* phase, int N, double km, double ki, double kc,

@@ -535,8 +535,9 @@ k_fx_inverse(GridDesc g, unsigned mask, const float2* __restrict__ spec, float* 
     constexpr bool kAddR = MODE == XI_ADD_R_RES || MODE == XI_ADD_R;
     const bool res = kRes && (g.dflags ? g.resid != 0 : true);
     const bool addr = kAddR && (g.dflags ? (g.dflags[slot] & SF_ADDR) != 0 : true);
+    const bool relax = g.relax != 0.0;   // relaxed schemes keep a fraction of the old field
     float2 old[E], radd[E];
-    if (res) s2_load<M>(old, out, t);
+    if (res || relax) s2_load<M>(old, out, t);
     if (addr) s2_load<M>(radd, reinterpret_cast<const float2*>(r32 + fbase), t);
     __shared__ float2 tws[2 * M];
     stage_twiddles<M>(tws, g);
@@ -544,8 +545,10 @@ k_fx_inverse(GridDesc g, unsigned mask, const float2* __restrict__ spec, float* 
     float2 v[E];
     row_inverse<M, TP, E>(v, t, sh + r * RS, spec + (long long)slot * 3 * g.NNM + row * M, tws, tws + M);
     float acc = 0.f;
+    const float wn = (float)(1.0 - g.relax), wo = (float)g.relax;
 #pragma unroll
     for (int j = 0; j < E; ++j) {
+        if (relax) v[j] = make_float2(wn * v[j].x + wo * old[j].x, wn * v[j].y + wo * old[j].y);
         if (addr) v[j] = make_float2(__fadd_rn(v[j].x, radd[j].x), __fadd_rn(v[j].y, radd[j].y));
         if (res) {
             const float da = v[j].x - old[j].x, db = v[j].y - old[j].y;
@@ -913,7 +916,8 @@ bool fast_x_inverse(const GridDesc& g, int mode, unsigned mask, const void* spec
 }
 
 bool chain_sweeps(const GridDesc& g) {
-    return !g.nochain && !(g.xyvar == 1 && fused_cluster(g.N)) && fast_x_ctas(g) > 0;
+    // a relaxed scheme needs the old field in every x inverse: its sweeps are not chained
+    return !g.nochain && g.relax == 0.0 && !(g.xyvar == 1 && fused_cluster(g.N)) && fast_x_ctas(g) > 0;
 }
 
 namespace {

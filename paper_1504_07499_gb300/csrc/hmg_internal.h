@@ -39,6 +39,11 @@ struct GridDesc {
     // basic scheme (field e, Y = (k - k0) / k0, W = k, KP = 1): ga = 0, gb = 1, gc = 1, epsf = 1.
     int scheme;
     double ga, gb, gc, epsf;
+    // Relaxed schemes of the Eyre-Milton family (augmented Lagrangian, polarization
+    // family with relaxation beta): the x inverse keeps this fraction of the old field,
+    // field^{n+1} = (1 - relax) T(field^n) + relax field^n, relax = 1 - beta / 2
+    // (0: no relaxation; the sweep is then the plain map T).
+    double relax;
     double E[kMaxSlots][3];  // macroscopic gradient of each right-hand side
     int nslots;            // right-hand sides held in the fields
     int rows;              // x-pass rows per CTA

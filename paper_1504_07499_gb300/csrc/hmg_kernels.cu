@@ -171,8 +171,14 @@ k_x_inverse(GridDesc g, unsigned mask, const typename Cplx<R>::T* __restrict__ s
     const bool resid = kRes && (g.dflags ? g.resid != 0 : true);
     const bool addr = kAddR && (g.dflags ? (g.dflags[slot] & SF_ADDR) != 0 : true);
     double acc = 0.0;
+    const bool relax = g.relax != 0.0;            // uniform: kernel argument
+    const R wn = R(1.0 - g.relax), wo = R(g.relax);
     for (int q = threadIdx.x; q < rows * M; q += blockDim.x) {
         T2 v = res[q];
+        if (relax) {   // relaxed schemes: (1 - relax) T(field) + relax field
+            const T2 o = out[q];
+            v = mk(wn * v.x + wo * o.x, wn * v.y + wo * o.y);
+        }
         if (MODE == XI_DIFF) {
             const T2 o = out[q];
             const double da = (double)v.x - (double)o.x, db = (double)v.y - (double)o.y;

@@ -69,7 +69,7 @@ struct SolveState {
 };
 
 GridDesc make_desc(const GridPlan& gp, bool fp64, const double k[3], const uint8_t* phase_d, int nslots,
-                   int scheme = HMG_SCHEME_EYRE_MILTON);
+                   int scheme = HMG_SCHEME_EYRE_MILTON, double beta = 2.0);
 
 // Pick the faster z-pass variant of the FP32 register-resident path for g.N by timing
 // both on the state's spectrum buffer (its contents are scratch); cached per context.

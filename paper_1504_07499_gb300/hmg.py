@@ -22,7 +22,7 @@ HMG_OK, HMG_PENDING = 0, 1
 HMG_INVALID_ARG, HMG_OUT_OF_MEMORY, HMG_NOT_CONVERGED = -1, -2, -3
 HMG_DIVERGED, HMG_CUDA_ERROR, HMG_BUSY, HMG_UNKNOWN_TICKET = -4, -5, -6, -7
 HMG_FP64, HMG_FP32_BULK = 0, 1
-HMG_SCHEME_EYRE_MILTON, HMG_SCHEME_BASIC = 0, 1
+HMG_SCHEME_EYRE_MILTON, HMG_SCHEME_BASIC, HMG_SCHEME_AUGMENTED_LAGRANGIAN = 0, 1, 2
 STATUS_NAMES = {0: "OK", 1: "PENDING", -1: "INVALID_ARG", -2: "OUT_OF_MEMORY", -3: "NOT_CONVERGED",
                 -4: "DIVERGED", -5: "CUDA_ERROR", -6: "BUSY", -7: "UNKNOWN_TICKET"}
 
@@ -31,7 +31,7 @@ EXPORTS = ["hmg_version", "hmg_last_error", "hmg_create", "hmg_destroy", "hmg_vo
            "hmg_solve_fields", "hmg_em_iterate", "hmg_equilibrium", "hmg_fft_forward", "hmg_fft_inverse",
            "hmg_solve_batch", "hmg_submit", "hmg_poll", "hmg_footprint", "hmg_trace_enable",
            "hmg_trace_read", "hmg_equilibrium_noalloc", "hmg_set_variant", "hmg_get_variant",
-           "hmg_server_stats", "hmg_solve_scheme"]
+           "hmg_server_stats", "hmg_solve_scheme", "hmg_solve_polarization"]
 HMG_NOALLOC_MAX_N = 64
 KERNEL_KINDS = ["x_forward", "y_forward", "z_green", "y_inverse", "x_inverse", "eq_x", "eq_z", "other",
                 "x_round", "fp64"]
@@ -78,6 +78,7 @@ def lib() -> C.CDLL:
         L.hmg_solve.argtypes = [vp, vp, i, d, d, d, d, i, i, dp, C.POINTER(hmg_info)]
         L.hmg_solve_fields.argtypes = [vp, vp, i, d, d, d, d, i, i, dp, C.POINTER(hmg_info), vp]
         L.hmg_solve_scheme.argtypes = [vp, vp, i, d, d, d, d, i, i, i, dp, C.POINTER(hmg_info), vp]
+        L.hmg_solve_polarization.argtypes = [vp, vp, i, d, d, d, d, i, d, i, dp, C.POINTER(hmg_info), vp]
         L.hmg_em_iterate.argtypes = [vp, vp, i, d, d, d, dp, i, i, vp, dp]
         L.hmg_equilibrium.argtypes = [vp, vp, i, d, d, d, i, vp, dp, dp]
         L.hmg_fft_forward.argtypes = [vp, i, i, i, vp, vp]
@@ -178,6 +179,16 @@ def hmg_solve_scheme(ctx: int, phase, N: int, k, tol: float, precision: int, sch
     info = hmg_info()
     st = lib().hmg_solve_scheme(ctx, _ptr(phase), N, k[0], k[1], k[2], tol, precision, scheme, max_iter, _dbuf(K),
                                 C.byref(info), _ptr(e_out) if e_out is not None else None)
+    _check(st, allow)
+    return K.reshape(3, 3), info.as_dict(), st
+
+
+def hmg_solve_polarization(ctx: int, phase, N: int, k, tol: float, precision: int, beta: float, e_out=None,
+                           max_iter: int = 0, allow=(HMG_OK,)):
+    K = np.zeros(9)
+    info = hmg_info()
+    st = lib().hmg_solve_polarization(ctx, _ptr(phase), N, k[0], k[1], k[2], tol, precision, beta, max_iter,
+                                      _dbuf(K), C.byref(info), _ptr(e_out) if e_out is not None else None)
     _check(st, allow)
     return K.reshape(3, 3), info.as_dict(), st
 
