@@ -134,6 +134,32 @@ hmg_status hmg_destroy(hmg_ctx* ctx);
 hmg_status hmg_voxelize(hmg_ctx* ctx, const hmg_sphere* spheres, size_t n, double layer,
                         int N, uint8_t* phase_out);
 
+/* Seeded placement of n identical, non-overlapping spheres of outer radius r in the
+ * periodic unit cube, computed on the GPU (§2: the RVEs come from random sequential
+ * adsorption, up to 100 spheres and 40 % volume fraction).  For n spheres filling a
+ * volume fraction f (coating included), r = (3 f / (4 pi n))^(1/3).
+ * Steps: RSA at radius r (candidates uniform in the cube, accepted in draw order when
+ * farther than 2r from every accepted centre, periodic minimum image); if it cannot
+ * place n spheres (RSA jams near 38 %), RSA at 0.85 r followed by Monte-Carlo
+ * displacement sweeps that grow the radius back to r.  Random numbers come from the
+ * counter-based SplitMix64 stream of `seed` (streams 0, 2 and 1 for the three steps);
+ * every squared distance is (dx^2 + dy^2) + dz^2 with each operation rounded on its own,
+ * so the result is reproducible bit for bit on any machine.
+ * max_candidates: RSA candidate cap (drawn in blocks of 8192, so up to the next multiple).
+ * spheres_out: n entries (host or device), radius r.  generator: NULL, or 0 (RSA) /
+ * 1 (reduced-radius RSA + growth sweeps).  Every loop is bounded (candidate cap, 20000
+ * growth sweeps).
+ * Errors: HMG_INVALID_ARG for n outside 1..1024, r outside (0, 0.5) or a cap below 1;
+ * HMG_NOT_CONVERGED when neither step places the spheres (nothing is written). */
+hmg_status hmg_rsa(hmg_ctx* ctx, uint64_t seed, int n, double r, long long max_candidates,
+                   hmg_sphere* spheres_out, int* generator);
+
+/* The RVE of §2 as a phase grid: hmg_rsa followed by hmg_voxelize with layer l.
+ * phase_out: N^3 bytes (host or device); spheres_out: NULL or n entries (host or
+ * device).  Errors as hmg_rsa and hmg_voxelize. */
+hmg_status hmg_rve(hmg_ctx* ctx, uint64_t seed, int n, double r, long long max_candidates, double layer,
+                   int N, uint8_t* phase_out, hmg_sphere* spheres_out, int* generator);
+
 /* Effective conductivity tensor of a three-phase grid (§3 Algorithm, steps 1-7, run
  * for the three unit gradients; §3 last paragraph for L_hom).
  * phase: N^3 bytes (host or device).  k_*: phase conductivities (> 0).
@@ -276,6 +302,15 @@ hmg_status hmg_solve_batch(hmg_ctx* ctx, int count, const uint8_t* const* phases
 hmg_status hmg_submit(hmg_ctx* ctx, const uint8_t* phase, int N, double k_matrix,
                       double k_incl, double k_coat, double tol, hmg_precision precision,
                       uint64_t* ticket);
+
+/* hmg_submit for an RVE that the request loop generates on the device when it admits
+ * the request: placement as hmg_rsa (seed, n spheres of outer radius r, candidate cap
+ * 400000), voxelization with layer l on an N^3 grid, then the solve -- no phase grid
+ * crosses the host.  A placement that fails finishes the request with its status
+ * (HMG_NOT_CONVERGED).  Errors as hmg_submit and hmg_rsa. */
+hmg_status hmg_submit_rve(hmg_ctx* ctx, uint64_t seed, int n, double r, double layer, int N,
+                          double k_matrix, double k_incl, double k_coat, double tol,
+                          hmg_precision precision, uint64_t* ticket);
 
 /* Result of a submitted request: HMG_PENDING while queued or running; otherwise the
  * request's final status with K_out (9 doubles, host) and info (nullable) filled in.

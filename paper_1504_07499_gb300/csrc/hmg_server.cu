@@ -48,6 +48,25 @@ hmg_status Server::submit(const uint8_t* phase, int N, const double k[3], double
     memcpy(r.k, k, sizeof(r.k));
     r.tol = tol;
     r.prec = p;
+    return enqueue(std::move(r), ticket);
+}
+
+hmg_status Server::submit_rve(uint64_t seed, int n, double radius, double layer, int N, const double k[3], double tol,
+                              hmg_precision p, uint64_t* ticket) {
+    Request r;
+    r.rve = true;
+    r.seed = seed;
+    r.n_spheres = n;
+    r.radius = radius;
+    r.layer = layer;
+    r.N = N;
+    memcpy(r.k, k, sizeof(r.k));
+    r.tol = tol;
+    r.prec = p;
+    return enqueue(std::move(r), ticket);
+}
+
+hmg_status Server::enqueue(Request&& r, uint64_t* ticket) {
     r.t_submit = now_s();
     std::lock_guard<std::mutex> lk(mu);
     if (queue.size() >= 4096) {
@@ -60,6 +79,30 @@ hmg_status Server::submit(const uint8_t* phase, int N, const double k[3], double
     queue.push_back(r.ticket);
     reqs.emplace(r.ticket, std::move(r));
     cv.notify_all();
+    return HMG_OK;
+}
+
+// Phase grid of a request: the caller's copy, or for an RVE request the device-generated
+// one (placement + voxelization on the loop's stream) in `dev`, which the caller frees.
+static hmg_status request_phase(hmg_ctx* ctx, Request* r, const uint8_t** phase, uint8_t** dev) {
+    *dev = nullptr;
+    if (!r->rve) {
+        *phase = r->phase.data();
+        return HMG_OK;
+    }
+    uint8_t* buf = (uint8_t*)ctx->alloc((size_t)r->N * r->N * r->N);
+    if (!buf) {
+        set_error("cannot allocate the RVE phase grid");
+        return HMG_OUT_OF_MEMORY;
+    }
+    int gen = 0;
+    hmg_status s = hmg_rve(ctx, r->seed, r->n_spheres, r->radius, 400000, r->layer, r->N, buf, nullptr, &gen);
+    if (s != HMG_OK) {
+        ctx->release(buf);
+        return s;
+    }
+    *phase = buf;
+    *dev = buf;
     return HMG_OK;
 }
 
@@ -138,9 +181,11 @@ void Server::loop() {
             }
             double K[9] = {0};
             hmg_info info{};
-            hmg_status s = cs != HMG_OK ? cs
-                                        : hmg_solve(ctx, r->phase.data(), r->N, r->k[0], r->k[1], r->k[2], r->tol,
-                                                    HMG_FP64, 0, K, &info);
+            const uint8_t* ph = nullptr;
+            uint8_t* dev = nullptr;
+            hmg_status s = cs != HMG_OK ? cs : request_phase(ctx, r, &ph, &dev);
+            if (s == HMG_OK) s = hmg_solve(ctx, ph, r->N, r->k[0], r->k[1], r->k[2], r->tol, HMG_FP64, 0, K, &info);
+            if (dev) ctx->release(dev);
             std::lock_guard<std::mutex> lk(mu);
             r->status = s == HMG_PENDING ? HMG_CUDA_ERROR : s;
             memcpy(r->K, K, sizeof(K));
@@ -156,7 +201,14 @@ void Server::loop() {
                 r = &reqs[t];
             }
             Entry* e = nullptr;
-            hmg_status s = cs != HMG_OK ? cs : eng->add((long long)t, r->phase.data(), r->N, r->k, r->tol, 0, &e);
+            const uint8_t* ph = nullptr;
+            uint8_t* dev = nullptr;
+            hmg_status s = cs != HMG_OK ? cs : request_phase(ctx, r, &ph, &dev);
+            if (s == HMG_OK) s = eng->add((long long)t, ph, r->N, r->k, r->tol, 0, &e);
+            if (dev) {   // the entry holds its own copy
+                cudaStreamSynchronize(ctx->stream);
+                ctx->release(dev);
+            }
             if (s != HMG_OK) {   // e.g. the caller's own solves hold the budget
                 std::lock_guard<std::mutex> lk(mu);
                 r->status = s;
@@ -208,6 +260,22 @@ void Server::loop() {
 
 using namespace hmg;
 
+namespace {
+// The context's request loop, started by the first submission (one loop even when
+// several threads submit first at once).  Starting it releases the context's own solve
+// state: the loop's requests draw on the same budget.
+Server* server_of(hmg_ctx* ctx) {
+    std::lock_guard<std::mutex> lk(ctx->server_mu);
+    if (!ctx->server) {
+        DeviceGuard dg(ctx->device);
+        cudaStreamSynchronize(ctx->stream);
+        ctx->solve.free_all(ctx);
+        ctx->server = new Server(ctx->device, ctx->pool);
+    }
+    return ctx->server;
+}
+}  // namespace
+
 extern "C" {
 
 hmg_status hmg_submit(hmg_ctx* ctx, const uint8_t* phase, int N, double km, double ki, double kc, double tol,
@@ -222,20 +290,25 @@ hmg_status hmg_submit(hmg_ctx* ctx, const uint8_t* phase, int N, double km, doub
         set_error("request footprint exceeds the context budget");
         return HMG_OUT_OF_MEMORY;
     }
-    Server* srv;
-    {
-        std::lock_guard<std::mutex> lk(ctx->server_mu);
-        if (!ctx->server) {
-            // the caller's solve state is released: the loop's requests draw on the same budget
-            DeviceGuard dg(ctx->device);
-            cudaStreamSynchronize(ctx->stream);
-            ctx->solve.free_all(ctx);
-            ctx->server = new Server(ctx->device, ctx->pool);
-        }
-        srv = ctx->server;
+    const double k[3] = {km, ki, kc};
+    return server_of(ctx)->submit(phase, N, k, tol, precision, ticket);
+}
+
+hmg_status hmg_submit_rve(hmg_ctx* ctx, uint64_t seed, int n, double r, double layer, int N, double km, double ki,
+                          double kc, double tol, hmg_precision precision, uint64_t* ticket) {
+    g_last_error.clear();
+    if (!ctx || !ticket || !valid_N(N) || !(km > 0 && ki > 0 && kc > 0) || !(tol > 0) ||
+        (precision != HMG_FP64 && precision != HMG_FP32_BULK) || n < 1 || n > 1024 || !(r > 0.0 && r < 0.5) ||
+        !(layer > 0.0 && layer < 1.0)) {
+        set_error("bad submit arguments");
+        return HMG_INVALID_ARG;
+    }
+    if (state_bytes(N, precision == HMG_FP64, 3) > ctx->budget) {
+        set_error("request footprint exceeds the context budget");
+        return HMG_OUT_OF_MEMORY;
     }
     const double k[3] = {km, ki, kc};
-    return srv->submit(phase, N, k, tol, precision, ticket);
+    return server_of(ctx)->submit_rve(seed, n, r, layer, N, k, tol, precision, ticket);
 }
 
 hmg_status hmg_server_stats(hmg_ctx* ctx, long long out[6]) {

@@ -26,6 +26,11 @@ struct Request {
     hmg_info info{};
     double t_submit = 0, t_start = 0, t_done = 0;
     bool admitted = false;
+    // RVE generated on the device at admission (hmg_submit_rve) instead of a phase grid
+    bool rve = false;
+    uint64_t seed = 0;
+    int n_spheres = 0;
+    double radius = 0, layer = 0;
 };
 
 struct Server {
@@ -33,6 +38,8 @@ struct Server {
     Server(int device, std::shared_ptr<BudgetPool> pool);
     ~Server();
     hmg_status submit(const uint8_t* phase, int N, const double k[3], double tol, hmg_precision p, uint64_t* ticket);
+    hmg_status submit_rve(uint64_t seed, int n, double r, double layer, int N, const double k[3], double tol,
+                          hmg_precision p, uint64_t* ticket);
     hmg_status poll(uint64_t ticket, double K[9], hmg_info* info);
     // counters: submitted, completed, most requests resident at once, engine ticks,
     // graph captures, graph launches
@@ -40,6 +47,7 @@ struct Server {
 
    private:
     void loop();
+    hmg_status enqueue(Request&& r, uint64_t* ticket);
     int device;
     std::shared_ptr<BudgetPool> pool;
     int max_slots = 64;

@@ -31,7 +31,8 @@ EXPORTS = ["hmg_version", "hmg_last_error", "hmg_create", "hmg_destroy", "hmg_vo
            "hmg_solve_fields", "hmg_em_iterate", "hmg_equilibrium", "hmg_fft_forward", "hmg_fft_inverse",
            "hmg_solve_batch", "hmg_submit", "hmg_poll", "hmg_footprint", "hmg_trace_enable",
            "hmg_trace_read", "hmg_equilibrium_noalloc", "hmg_set_variant", "hmg_get_variant",
-           "hmg_server_stats", "hmg_solve_scheme", "hmg_solve_polarization"]
+           "hmg_server_stats", "hmg_solve_scheme", "hmg_solve_polarization", "hmg_rsa", "hmg_rve",
+           "hmg_submit_rve"]
 HMG_NOALLOC_MAX_N = 64
 KERNEL_KINDS = ["x_forward", "y_forward", "z_green", "y_inverse", "x_inverse", "eq_x", "eq_z", "other",
                 "x_round", "fp64"]
@@ -75,6 +76,8 @@ def lib() -> C.CDLL:
         L.hmg_create.argtypes = [C.POINTER(vp), i, sz]
         L.hmg_destroy.argtypes = [vp]
         L.hmg_voxelize.argtypes = [vp, vp, sz, d, i, vp]
+        L.hmg_rsa.argtypes = [vp, C.c_uint64, i, d, C.c_longlong, vp, C.POINTER(i)]
+        L.hmg_rve.argtypes = [vp, C.c_uint64, i, d, C.c_longlong, d, i, vp, vp, C.POINTER(i)]
         L.hmg_solve.argtypes = [vp, vp, i, d, d, d, d, i, i, dp, C.POINTER(hmg_info)]
         L.hmg_solve_fields.argtypes = [vp, vp, i, d, d, d, d, i, i, dp, C.POINTER(hmg_info), vp]
         L.hmg_solve_scheme.argtypes = [vp, vp, i, d, d, d, d, i, i, i, dp, C.POINTER(hmg_info), vp]
@@ -86,6 +89,7 @@ def lib() -> C.CDLL:
         L.hmg_solve_batch.argtypes = [vp, i, C.POINTER(vp), C.POINTER(i), dp, d, i, i, dp, C.POINTER(hmg_info)]
         L.hmg_submit.argtypes = [vp, vp, i, d, d, d, d, i, C.POINTER(C.c_uint64)]
         L.hmg_poll.argtypes = [vp, C.c_uint64, dp, C.POINTER(hmg_info)]
+        L.hmg_submit_rve.argtypes = [vp, C.c_uint64, i, d, d, i, d, d, d, d, i, C.POINTER(C.c_uint64)]
         L.hmg_equilibrium_noalloc.argtypes = [vp, i, d, d, d, vp, dp, dp]
         L.hmg_server_stats.argtypes = [vp, C.POINTER(C.c_longlong)]
         L.hmg_set_variant.argtypes = [vp, i, i]
@@ -152,6 +156,24 @@ def hmg_voxelize(ctx: int, spheres, layer: float, N: int, phase_out) -> None:
     """spheres: (n, 4) float64 array (cx, cy, cz, r) or device tensor; phase_out: N^3 uint8."""
     n = spheres.shape[0]
     _check(lib().hmg_voxelize(ctx, _ptr(spheres), n, layer, N, _ptr(phase_out)))
+
+
+def hmg_rsa(ctx: int, seed: int, n: int, r: float, max_candidates: int = 400_000, spheres_out=None):
+    """Device sphere placement; returns ((n, 4) spheres, generator) -- spheres_out (host
+    array or device tensor of n x 4 doubles) is filled when given."""
+    out = spheres_out if spheres_out is not None else np.empty((n, 4))
+    gen = C.c_int(-1)
+    _check(lib().hmg_rsa(ctx, seed, n, r, max_candidates, _ptr(out), C.byref(gen)))
+    return out, gen.value
+
+
+def hmg_rve(ctx: int, seed: int, n: int, r: float, layer: float, N: int, phase_out, spheres_out=None,
+            max_candidates: int = 400_000):
+    """Device sphere placement + voxelization into phase_out (N^3 bytes); returns the generator."""
+    gen = C.c_int(-1)
+    _check(lib().hmg_rve(ctx, seed, n, r, max_candidates, layer, N, _ptr(phase_out),
+                         _ptr(spheres_out) if spheres_out is not None else None, C.byref(gen)))
+    return gen.value
 
 
 def hmg_solve(ctx: int, phase, N: int, k, tol: float, precision: int, max_iter: int = 0,
@@ -242,6 +264,13 @@ def hmg_solve_batch(ctx: int, phases, N_list, k3, tol: float, precision: int, ma
 def hmg_submit(ctx: int, phase, N: int, k, tol: float, precision: int) -> int:
     t = C.c_uint64()
     _check(lib().hmg_submit(ctx, _ptr(phase), N, k[0], k[1], k[2], tol, precision, C.byref(t)))
+    return t.value
+
+
+def hmg_submit_rve(ctx: int, seed: int, n: int, r: float, layer: float, N: int, k, tol: float,
+                   precision: int) -> int:
+    t = C.c_uint64()
+    _check(lib().hmg_submit_rve(ctx, seed, n, r, layer, N, k[0], k[1], k[2], tol, precision, C.byref(t)))
     return t.value
 
 

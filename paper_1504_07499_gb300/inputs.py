@@ -65,10 +65,25 @@ def sphere_radius(n: int, f: float) -> float:
 
 
 def _min_image_sq(a: np.ndarray, b: np.ndarray) -> np.ndarray:
-    """Squared periodic minimum-image distances between rows of ``a`` (k,3) and ``b`` (m,3)."""
+    """Squared periodic minimum-image distances between rows of ``a`` (k,3) and ``b`` (m,3).
+    Every operation rounds on its own in a fixed order, (dx^2 + dy^2) + dz^2 with
+    d = min(|a - b|, 1 - |a - b|), so the value is the same on every platform (and on
+    the GPU generator, which follows the same steps)."""
     d = np.abs(a[:, None, :] - b[None, :, :])
     d = np.minimum(d, 1.0 - d)
-    return np.einsum("kmj,kmj->km", d, d)
+    return (d[..., 0] * d[..., 0] + d[..., 1] * d[..., 1]) + d[..., 2] * d[..., 2]
+
+
+def _wrap1(x: np.ndarray) -> np.ndarray:
+    """x wrapped into [0, 1): the exact remainder fmod(x, 1), plus 1 (one rounding) where
+    it is negative; a zero remainder is +0."""
+    m = np.fmod(x, 1.0)
+    return np.where(m < 0.0, m + 1.0, m) + 0.0
+
+
+def _sq(x: float) -> float:
+    """x * x (a single rounded product, unlike pow)."""
+    return x * x
 
 
 def rsa(seed: int, n: int, r: float, max_candidates: int = 2_000_000,
@@ -78,7 +93,7 @@ def rsa(seed: int, n: int, r: float, max_candidates: int = 2_000_000,
     (n, 3) centres, or None when ``max_candidates`` draws do not place ``n`` spheres."""
     rng = SplitMix64(seed, stream)
     acc = np.empty((0, 3))
-    lim = (2.0 * r) ** 2
+    lim = _sq(2.0 * r)
     used = 0
     while used < max_candidates:
         cand = rng.uniform(3 * batch).reshape(batch, 3)
@@ -117,13 +132,13 @@ def grow_mc(seed: int, centres: np.ndarray, r_target: float, max_sweeps: int = 2
         d2 = _min_image_sq(c, c)
         np.fill_diagonal(d2, np.inf)
         r_work = min(r_target, 0.5 * math.sqrt(d2.min()))
-        if r_work >= r_target and d2.min() > (2.0 * r_target) ** 2:
+        if r_work >= r_target and d2.min() > _sq(2.0 * r_target):
             return c
         step = max(0.25 * r_target, 1e-3)
         u = rng.uniform(4 * n).reshape(n, 4)
-        lim = (2.0 * r_work) ** 2
+        lim = _sq(2.0 * r_work)
         for i in range(n):
-            trial = (c[i] + step * (2.0 * u[i, :3] - 1.0)) % 1.0
+            trial = _wrap1(c[i] + step * (2.0 * u[i, :3] - 1.0))
             others = np.delete(c, i, axis=0)
             if (_min_image_sq(trial[None, :], others)[0] > lim).all():
                 c[i] = trial
