@@ -291,11 +291,15 @@ hmg_status hmg_solve_batch(hmg_ctx* ctx, int count, const uint8_t* const* phases
  * queued ones while their footprint (hmg_footprint) fits the context's budget, up to
  * 64 at once; every tick advances all admitted HMG_FP32_BULK requests together in one
  * CUDA-graph launch (continuous batching).  HMG_FP64 requests run one at a time.
+ * Grids of 192^3 voxels and more and smaller grids run in two lanes (each a worker
+ * thread with its own streams and engine), so small requests do not wait for the ticks
+ * of large ones and the kernels of both lanes share the GPU.
  * The loop and the caller's context share one budget: the first hmg_submit on a
  * context releases the context's own solve state, and device memory that later calls
  * on the context hold counts against the loop's admissions (a request that cannot get
- * its state then finishes with HMG_OUT_OF_MEMORY).  The first hmg_submit starts the
- * loop; concurrent first calls start one loop.
+ * its state waits in the queue while other requests or the caller hold memory, and
+ * finishes with HMG_OUT_OF_MEMORY after about 10 s of waiting).  The first hmg_submit
+ * starts the loop; concurrent first calls start one loop.
  * *ticket identifies the request.
  * Returns HMG_BUSY when the queue is full, HMG_INVALID_ARG for bad arguments, and
  * HMG_OUT_OF_MEMORY when the request alone exceeds the budget. */

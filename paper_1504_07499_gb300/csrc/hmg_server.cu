@@ -1,5 +1,5 @@
-// Request loop behind hmg_submit / hmg_poll: a worker thread with its own context
-// runs queued requests.
+// Request loop behind hmg_submit / hmg_poll: two lanes (large and small grids), each a
+// worker thread with its own context and streams, run the queued requests.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -18,7 +18,7 @@ static double now_s() {
 }
 
 Server::Server(int dev, std::shared_ptr<BudgetPool> p) : device(dev), pool(std::move(p)) {
-    worker = std::thread([this] { loop(); });
+    for (int l = 0; l < kLanes; ++l) workers[l] = std::thread([this, l] { loop(l); });
 }
 
 Server::~Server() {
@@ -27,7 +27,8 @@ Server::~Server() {
         stop = true;
     }
     cv.notify_all();
-    if (worker.joinable()) worker.join();
+    for (auto& w : workers)
+        if (w.joinable()) w.join();
 }
 
 hmg_status Server::submit(const uint8_t* phase, int N, const double k[3], double tol, hmg_precision p,
@@ -69,6 +70,7 @@ hmg_status Server::submit_rve(uint64_t seed, int n, double radius, double layer,
 hmg_status Server::enqueue(Request&& r, uint64_t* ticket) {
     r.t_submit = now_s();
     std::lock_guard<std::mutex> lk(mu);
+    std::deque<uint64_t>& queue = queues[lane_of(r.N)];
     if (queue.size() >= 4096) {
         set_error("request queue full");
         return HMG_BUSY;
@@ -121,10 +123,7 @@ hmg_status Server::poll(uint64_t ticket, double K[9], hmg_info* info) {
     return s;
 }
 
-// Continuous batching: every engine tick advances all admitted FP32-bulk requests
-// together; between ticks, finished requests retire (their device state is freed)
-// and queued ones are admitted while their footprint fits the context budget.
-// FP64 requests run one at a time with the plain method.
+// Request-loop counters (summed over the lanes).
 void Server::stats(long long out[6]) {
     std::lock_guard<std::mutex> lk(mu);
     out[0] = n_submitted;
@@ -135,23 +134,37 @@ void Server::stats(long long out[6]) {
     out[5] = n_launches;
 }
 
-void Server::loop() {
+int Server::lane_of(int N) { return (long long)N * N * N >= kLargeN3 ? 0 : 1; }
+
+// One lane of the request loop.  Continuous batching: every engine tick advances all
+// admitted FP32-bulk requests of the lane together; between ticks, finished requests retire
+// (their device state is freed) and queued ones are admitted while their footprint fits the
+// budget.  FP64 requests run one at a time with the plain method.  The lanes (large and
+// small grids) run on their own threads, contexts and streams, so a small request's ticks
+// do not wait for a large one's and the two lanes' kernels share the GPU; they draw on one
+// budget, and a request whose state does not fit while others hold memory waits in its
+// queue.
+void Server::loop(int lane) {
     hmg_ctx* ctx = nullptr;
     hmg_status cs = hmg_create(&ctx, device, pool->limit);
     std::unique_ptr<Engine> eng;
     if (cs == HMG_OK) {
-        ctx->pool = pool;   // one budget for the caller's context and this loop
+        ctx->pool = pool;   // one budget for the caller's context and every lane
         cudaSetDevice(device);
         eng = std::make_unique<Engine>(ctx, ctx->stream, ctx->stream64, true);
     }
+    std::deque<uint64_t>& queue = queues[lane];
     std::map<Entry*, uint64_t> running;
+    bool backoff = false;
     for (;;) {
         std::vector<uint64_t> admit, fp64;
         {
             std::unique_lock<std::mutex> lk(mu);
+            if (backoff && running.empty())   // waiting for memory another lane or the caller holds
+                cv.wait_for(lk, std::chrono::milliseconds(2), [&] { return stop; });
             cv.wait(lk, [&] { return stop || !queue.empty() || !running.empty(); });
             if (stop) break;
-            // device memory held by the caller's context and by this loop together
+            // device memory held by the caller's context and by every lane together
             size_t used = pool->used.load();
             while (!queue.empty()) {
                 Request& r = reqs[queue.front()];
@@ -163,8 +176,8 @@ void Server::loop() {
                 }
                 const size_t need = state_bytes(r.N, false, 3);
                 if ((int)running.size() + (int)admit.size() >= max_slots) break;
-                // the first request of an idle loop is always admitted (it fits the budget
-                // by the check in hmg_submit); later ones while their footprint fits
+                // the first request of an idle lane is always tried (it fits the budget
+                // alone by the check in hmg_submit); later ones while their footprint fits
                 if ((!running.empty() || !admit.empty()) && used + need > (size_t)(0.95 * (double)pool->limit)) break;
                 used += need;
                 admit.push_back(r.ticket);
@@ -173,6 +186,14 @@ void Server::loop() {
             for (uint64_t t : admit) reqs[t].t_start = now_s();
             for (uint64_t t : fp64) reqs[t].t_start = now_s();
         }
+        backoff = false;
+        // a request that cannot get its state while others hold memory goes back to the
+        // front of the queue (at most kOomRetries times, then it fails)
+        auto retry = [&](Request* r, hmg_status s) {
+            if (s != HMG_OUT_OF_MEMORY || ++r->oom_retries > kOomRetries) return false;
+            return !running.empty() || pool->used.load() > 0;
+        };
+        std::vector<uint64_t> requeue;
         for (uint64_t t : fp64) {
             Request* r;
             {
@@ -186,6 +207,10 @@ void Server::loop() {
             hmg_status s = cs != HMG_OK ? cs : request_phase(ctx, r, &ph, &dev);
             if (s == HMG_OK) s = hmg_solve(ctx, ph, r->N, r->k[0], r->k[1], r->k[2], r->tol, HMG_FP64, 0, K, &info);
             if (dev) ctx->release(dev);
+            if (retry(r, s)) {
+                requeue.push_back(t);
+                continue;
+            }
             std::lock_guard<std::mutex> lk(mu);
             r->status = s == HMG_PENDING ? HMG_CUDA_ERROR : s;
             memcpy(r->K, K, sizeof(K));
@@ -194,7 +219,8 @@ void Server::loop() {
             r->info.seconds = r->t_done - r->t_submit;
             ++n_completed;
         }
-        for (uint64_t t : admit) {
+        for (size_t a = 0; a < admit.size(); ++a) {
+            const uint64_t t = admit[a];
             Request* r;
             {
                 std::lock_guard<std::mutex> lk(mu);
@@ -209,7 +235,11 @@ void Server::loop() {
                 cudaStreamSynchronize(ctx->stream);
                 ctx->release(dev);
             }
-            if (s != HMG_OK) {   // e.g. the caller's own solves hold the budget
+            if (retry(r, s)) {
+                requeue.insert(requeue.end(), admit.begin() + a, admit.end());
+                break;
+            }
+            if (s != HMG_OK) {
                 std::lock_guard<std::mutex> lk(mu);
                 r->status = s;
                 r->t_done = now_s();
@@ -219,17 +249,25 @@ void Server::loop() {
             }
             running[e] = t;
         }
+        if (!requeue.empty()) {
+            std::lock_guard<std::mutex> lk(mu);
+            for (auto it = requeue.rbegin(); it != requeue.rend(); ++it) queue.push_front(*it);
+            backoff = true;
+        }
         if (running.empty()) continue;
         {
             std::lock_guard<std::mutex> lk(mu);
-            max_resident = std::max(max_resident, (long long)running.size());
+            resident[lane] = (long long)running.size();
+            max_resident = std::max(max_resident, resident[0] + resident[1]);
         }
+        const int cap0 = eng->graph_captures;
+        const long long gl0 = eng->graph_launches;
         hmg_status s = eng->tick();
         {
             std::lock_guard<std::mutex> lk(mu);
             ++n_ticks;
-            n_captures = eng->graph_captures;
-            n_launches = eng->graph_launches;
+            n_captures += eng->graph_captures - cap0;
+            n_launches += eng->graph_launches - gl0;
         }
         std::vector<Entry*> done;
         for (auto& kv : running)
@@ -251,6 +289,8 @@ void Server::loop() {
             running.erase(e);
             eng->remove(e);
         }
+        std::lock_guard<std::mutex> lk(mu);
+        resident[lane] = (long long)running.size();
     }
     eng.reset();
     if (ctx) hmg_destroy(ctx);

@@ -27,6 +27,7 @@ struct Request {
     double t_submit = 0, t_start = 0, t_done = 0;
     bool admitted = false;
     // RVE generated on the device at admission (hmg_submit_rve) instead of a phase grid
+    int oom_retries = 0;    // admissions put back for lack of memory
     bool rve = false;
     uint64_t seed = 0;
     int n_spheres = 0;
@@ -46,18 +47,24 @@ struct Server {
     void stats(long long out[6]);
 
    private:
-    void loop();
+    // lane 0: grids of at least kLargeN3 voxels (192^3 and up); lane 1: smaller grids
+    static constexpr int kLanes = 2;
+    static constexpr long long kLargeN3 = 192LL * 192 * 192;
+    static constexpr int kOomRetries = 5000;   // ~10 s of 2 ms waits for memory to free up
+    static int lane_of(int N);
+    void loop(int lane);
     hmg_status enqueue(Request&& r, uint64_t* ticket);
     int device;
     std::shared_ptr<BudgetPool> pool;
     int max_slots = 64;
     std::mutex mu;
     std::condition_variable cv;
-    std::deque<uint64_t> queue;
+    std::deque<uint64_t> queues[kLanes];
     std::map<uint64_t, Request> reqs;
     uint64_t next = 1;
     bool stop = false;
-    std::thread worker;
+    std::thread workers[kLanes];
+    long long resident[kLanes] = {0, 0};
     long long n_submitted = 0, n_completed = 0, max_resident = 0, n_ticks = 0, n_captures = 0, n_launches = 0;
 };
 

@@ -123,3 +123,22 @@ def test_poll_unknown_ticket(ctx):
     with pytest.raises(hmg.HmgError) as e:
         hmg.hmg_poll(ctx.handle, 987654321)
     assert e.value.status == hmg.HMG_UNKNOWN_TICKET
+
+
+def test_small_requests_do_not_wait_for_a_large_one(ctx):
+    """Large (192^3 and up) and small grids run in separate lanes of the request loop:
+    small requests submitted after a large one finish first, and every result equals the
+    single solve of its grid."""
+    big_ph = om.voxelize(I.generate_spheres(3000, 100, 0.40).spheres, 0.3, 192)
+    small = [(ph, N, k) for ph, N, k in _rves() if N == 64]
+    with hmg.Context(0) as c:
+        tb = hmg.hmg_submit(c.handle, big_ph, 192, I.K_PHASES, 1e-8, hmg.HMG_FP32_BULK)
+        ts = [hmg.hmg_submit(c.handle, ph, N, k, 1e-8, hmg.HMG_FP32_BULK) for ph, N, k in small]
+        res = _wait(c.handle, [tb] + ts)
+    assert all(res[t][0] == hmg.HMG_OK for t in [tb] + ts)
+    assert max(res[t][2]["seconds"] for t in ts) < res[tb][2]["seconds"]
+    Kb, _, _ = ctx.solve(big_ph, I.K_PHASES, 1e-8, hmg.HMG_FP32_BULK)
+    assert kerr(res[tb][1], Kb) < 1e-5
+    for (ph, N, k), t in zip(small, ts):
+        Ks, _, _ = ctx.solve(ph, k, 1e-8, hmg.HMG_FP32_BULK)
+        assert kerr(res[t][1], Ks) < 1e-5
