@@ -337,8 +337,12 @@ hmg_status hmg_poll(hmg_ctx* ctx, uint64_t ticket, double K_out[9], hmg_info* in
  *          row block (0) or as a persistent kernel (1) whose CTAs stage the spectrum
  *          and phase rows of their next row block in shared memory with bulk copies
  *          while they transform the current one (bit-identical results).
- * The autotuner chooses bits 0, 1 and 3 and leaves bit 2 clear.  hmg_set_variant pins
- * `variant` (0 .. 15) for size N, or clears the choice (-1) so that the next solve
+ *   bit 4: with bit 0 clear, the z pass of plain and correction sweeps runs as a
+ *          persistent kernel whose CTAs stage the next column block (three tiled tensor
+ *          copies) in shared memory while they transform the current one (sizes up to
+ *          256; bit-identical results).
+ * The autotuner chooses bits 0, 1, 3 and 4 and leaves bit 2 clear.  hmg_set_variant pins
+ * `variant` (0 .. 31) for size N, or clears the choice (-1) so that the next solve
  * times them again.  All give the same results to rounding. */
 hmg_status hmg_set_variant(hmg_ctx* ctx, int N, int variant);
 

@@ -216,14 +216,23 @@ int autotune_z(::hmg_ctx* c, GridDesc g, SolveState* s, cudaStream_t st) {
     cudaMemsetAsync(s->spec32, 0, bytes, st);
     cudaMemsetAsync(s->f32buf, 0, bytes, st);
     // z pass: two kernels
-    int zbest = 0;
+    int zbest = 0, zpbest = 0;
     if (fast_z_ctas(g)) {
-        float zms[2];
-        for (int v = 0; v < 2; ++v) {
-            g.zvar = v;
+        // three z kernels: components in one thread, per-component groups, and the first
+        // as a persistent kernel with staged columns
+        float zms[3];
+        for (int v = 0; v < 3; ++v) {
+            g.zvar = v == 1 ? 1 : 0;
+            g.zpers = v == 2 ? 1 : 0;
             zms[v] = time_launches(st, [&] { launch_z_pass<float>(g, Z_ITER, all, s->spec32, nullptr, st); }, 4);
         }
-        zbest = zms[1] < zms[0] ? 1 : 0;
+        int b = 0;
+        for (int v = 1; v < 3; ++v)
+            if (zms[v] < zms[b]) b = v;
+        if (b == 2 && fast_take_wait_failure()) b = 0;
+        zbest = b == 1 ? 1 : 0;
+        zpbest = b == 2 ? 1 : 0;
+        g.zpers = 0;
     }
     // x and y passes: fused cluster kernels or separate passes
     int xybest = 0;
@@ -258,7 +267,7 @@ int autotune_z(::hmg_ctx* c, GridDesc g, SolveState* s, cudaStream_t st) {
         if (fast_take_wait_failure()) xpbest = 0;
     }
     cudaGetLastError();
-    best = zbest | (xybest << 1) | (xpbest << 3);
+    best = zbest | (xybest << 1) | (xpbest << 3) | (zpbest << 4);
     c->ztune[g.N] = best;
     return best;
 }
@@ -750,7 +759,7 @@ hmg_status Solver::run_bulk(int max_iter, double tol, hmg_info* info, double K[9
     }
     cudaEventDestroy(ready);
     if (err != HMG_OK) return err;
-    if (g.xpers && fast_take_wait_failure()) {
+    if ((g.xpers || g.zpers) && fast_take_wait_failure()) {
         set_error("a persistent kernel gave up waiting for its bulk copies; results are invalid");
         return HMG_CUDA_ERROR;
     }

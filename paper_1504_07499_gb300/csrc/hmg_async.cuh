@@ -42,6 +42,16 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t
         : "memory");
 }
 
+// Tiled 4D tensor copy (the tensor map describes the global array and the box) to this
+// CTA's shared memory at dst, completing on barrier mb.  x is the innermost coordinate.
+__device__ __forceinline__ void tensor_g2s_4d(uint32_t dst, const void* map, int x, int y, int z, int w, uint32_t mb) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
+        "%5}], [%6];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(w), "r"(mb)
+        : "memory");
+}
+
 __device__ __forceinline__ bool mbar_try(uint32_t mb, uint32_t parity) {
     uint32_t ok;
     asm volatile(

@@ -73,6 +73,7 @@ hmg_status prepare(hmg_ctx* ctx, const uint8_t* phase, int N, const double k[3],
         g->xyvar = (v >> 1) & 1;
         g->nochain = (v >> 2) & 1;
         g->xpers = (v >> 3) & 1;
+        g->zpers = (v >> 4) & 1;
     }
     if (g->relax != 0.0) {   // relaxed schemes read the old field in every x inverse
         g->xyvar = 0;
@@ -148,8 +149,8 @@ size_t hmg_footprint(int N, hmg_precision p) { return state_bytes(N, p == HMG_FP
 
 hmg_status hmg_set_variant(hmg_ctx* ctx, int N, int variant) {
     g_last_error.clear();
-    if (!ctx || !valid_N(N) || variant < -1 || variant > 15) {
-        set_error("bad context, N or variant (-1 .. 15)");
+    if (!ctx || !valid_N(N) || variant < -1 || variant > 31) {
+        set_error("bad context, N or variant (-1 .. 31)");
         return HMG_INVALID_ARG;
     }
     if (variant < 0) ctx->ztune.erase(N);
@@ -464,6 +465,7 @@ static hmg_status fft_common(hmg_ctx* ctx, int N, int count, hmg_precision preci
         g.xyvar = (v >> 1) & 1;
         g.nochain = (v >> 2) & 1;
         g.xpers = (v >> 3) & 1;
+        g.zpers = (v >> 4) & 1;
     }
     SolveState& s = ctx->solve;
     const long long N3 = g.N3;

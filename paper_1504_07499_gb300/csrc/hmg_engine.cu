@@ -111,6 +111,7 @@ hmg_status Engine::add(long long id, const uint8_t* phase, int N, const double k
         e->g.xyvar = (v >> 1) & 1;
         e->g.nochain = (v >> 2) & 1;
         e->g.xpers = (v >> 3) & 1;
+        e->g.zpers = (v >> 4) & 1;
     }
     launch_init_tau<float>(e->g, 7u, e->st.f32buf, st);
     e->index = (int)entries.size();
@@ -269,7 +270,7 @@ hmg_status Engine::tick_launch_and_update() {
     if (s == HMG_OK) s = cerr(cudaStreamSynchronize(st64), "FP64 work");
     if (s != HMG_OK) return s;
     bool pers = false;
-    for (auto& up : entries) pers = pers || up->g.xpers;
+    for (auto& up : entries) pers = pers || up->g.xpers || up->g.zpers;
     if (any32 && pers && fast_take_wait_failure()) {
         set_error("a persistent kernel gave up waiting for its bulk copies; results are invalid");
         return HMG_CUDA_ERROR;

@@ -15,7 +15,9 @@
 // threads, so every warp access is a run of contiguous bytes.
 // Within a block of FP32 sweeps the x inverse of one sweep and the x forward of the next
 // are one kernel (k_fx_round); the y and z passes are the same in every sweep.
+#include <cuda.h>
 #include <cuda_runtime.h>
+#include <cudaTypedefs.h>
 #include <stdint.h>
 
 #include <algorithm>
@@ -28,6 +30,10 @@
 
 namespace hmg {
 namespace fast {
+
+// Set by a persistent kernel whose bounded wait for a bulk copy gave up (read and
+// cleared by fast_take_wait_failure).
+__device__ unsigned g_wait_fail;
 
 // ---------------------------------------------------------------------------
 // y pass: P consecutive kx columns of one (component, z) plane; threads (p, t)
@@ -173,6 +179,102 @@ k_fz3(GridDesc g, unsigned mask, float2* __restrict__ spec, double* __restrict__
     for (int c = 0; c < 3; ++c)
 #pragma unroll
         for (int n1 = 0; n1 < E; ++n1) base[c * NNM + (long long)(TP * n1 + t) * rowz] = v[c][n1];
+}
+
+// Variant 0 as a persistent kernel: each CTA walks the (slot, ky, column block) items in
+// a fixed stride over the grid; while one item is transformed, the bulk-copy engine
+// stages the next item's three component columns (a tiled tensor copy each: P kx by all
+// kz at one ky) in shared memory, so HBM reads overlap the arithmetic.  Plain and
+// correction sweeps only (Z_ITER, Z_ITER_NOB); same float operations as k_fz3.
+template <int L, int P>
+struct ZSmem {
+    static constexpr size_t stage_bytes = (size_t)3 * L * P * sizeof(float2);
+    static constexpr size_t x_off = (stage_bytes + 127) / 128 * 128;
+    static constexpr size_t total = x_off + (size_t)3 * xslots<L>() * P * sizeof(float2);
+};
+
+template <int L, int P, int MODE>
+__global__ void __launch_bounds__(P * Split<L>::TP, 2)
+k_fz3_p(const __grid_constant__ CUtensorMap zmap, GridDesc g, unsigned mask, float2* __restrict__ spec, int nper) {
+    constexpr int E = Split<L>::E, TP = Split<L>::TP, KPT = E / TP;
+    constexpr int NS = xslots<L>() * P;
+    constexpr int N = L, M = L / 2;
+    constexpr long long NNM = (long long)N * N * M;
+    constexpr long long rowz = (long long)N * M;     // stride between z rows
+    using Z = ZSmem<L, P>;
+    extern __shared__ __align__(128) unsigned char dsm[];
+    const float2* stg = reinterpret_cast<const float2*>(dsm);   // [component][kz][column]
+    float2* sh = reinterpret_cast<float2*>(dsm + Z::x_off);      // 3 * NS
+    __shared__ __align__(8) unsigned long long mbar;
+    __shared__ int s_ok;
+    const int p = threadIdx.x % P, t = threadIdx.x / P;
+    const int nkb = M / P;
+    const int nitems = g.nslots * nper;
+    int item = blockIdx.x;
+    while (item < nitems && !slot_active(g, mask, item / nper)) item += gridDim.x;
+    if (item >= nitems) return;
+    const uint32_t mb = async::smem_addr(&mbar);
+    if (threadIdx.x == 0) async::mbar_init(mb);
+    auto issue = [&](int it) {   // thread 0: the three component columns of item `it`
+        const int slot = it / nper, b = it % nper;
+        async::mbar_expect(mb, (uint32_t)Z::stage_bytes);
+        for (int c = 0; c < 3; ++c)
+            async::tensor_g2s_4d(async::smem_addr(stg + c * L * P), &zmap, (b % nkb) * P, b / nkb, 0, slot * 3 + c, mb);
+    };
+    if (threadIdx.x == 0) issue(item);
+    __syncthreads();
+    const float2* twL = g.tw32 + g.pN.tw_off;
+    const float scale = (float)(1.0 / (double)g.N3);
+    const float ga = (float)g.ga, gb = (float)g.gb;
+    uint32_t parity = 0;
+    while (item < nitems) {
+        const int slot = item / nper, b = item % nper;
+        const int kb = b % nkb, ky = b / nkb;
+        const int kx = kb * P + p;
+        if (threadIdx.x == 0) s_ok = async::mbar_wait(mb, parity) ? 1 : 0;
+        __syncthreads();
+        if (!s_ok) {
+            if (threadIdx.x == 0) atomicOr(&g_wait_fail, 1u);
+            return;
+        }
+        async::mbar_wait(mb, parity);   // complete already: the copied bytes are visible here
+        parity ^= 1u;
+        float2 v[3][E];
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int n1 = 0; n1 < E; ++n1) v[c][n1] = stg[(c * L + TP * n1 + t) * P + p];
+        __syncthreads();   // every thread holds its columns: the staging takes the next item
+        int nxt = item + gridDim.x;
+        while (nxt < nitems && !slot_active(g, mask, nxt / nper)) nxt += gridDim.x;
+        if (threadIdx.x == 0 && nxt < nitems) issue(nxt);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) stage1_write<L, true>(v[c], t, twL, sh + c * NS + p, P);
+        __syncthreads();
+#pragma unroll
+        for (int c = 0; c < 3; ++c) stage2_read<L, true>(v[c], t, sh + c * NS + p, P);
+        const bool addb = g.dflags ? (g.dflags[slot] & SF_ADDB) != 0 : MODE == Z_ITER;
+        const float cE[3] = {(float)(g.gc * g.E[slot][0]), (float)(g.gc * g.E[slot][1]), (float)(g.gc * g.E[slot][2])};
+#pragma unroll
+        for (int i = 0; i < KPT; ++i)
+#pragma unroll
+            for (int k2 = 0; k2 < TP; ++k2)
+                green_mode_fast(kx, ky, t * KPT + i + E * k2, N, scale, ga, gb, addb, cE, v[0][i * TP + k2],
+                                v[1][i * TP + k2], v[2][i * TP + k2]);
+        __syncthreads();   // every thread has read the forward exchange
+#pragma unroll
+        for (int c = 0; c < 3; ++c) rstage2_write<L>(v[c], t, twL, sh + c * NS + p, P);
+        __syncthreads();
+#pragma unroll
+        for (int c = 0; c < 3; ++c) rstage1_read<L>(v[c], t, sh + c * NS + p, P);
+        float2* base = spec + (long long)slot * 3 * NNM + (long long)ky * M + kb * P + p;
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int n1 = 0; n1 < E; ++n1) base[c * NNM + (long long)(TP * n1 + t) * rowz] = v[c][n1];
+        __syncthreads();   // the exchange buffer and s_ok are reused by the next item
+        item = nxt;
+    }
 }
 
 // Variant 1: three thread groups, one per component; the projection d . s is summed
@@ -612,10 +714,6 @@ k_fx_round(GridDesc g, unsigned mask, float2* __restrict__ spec, float* __restri
     row_forward_split<M, TP, E>(v, t, rs, twM, twN, sp);
 }
 
-// Set by a persistent kernel whose bounded wait for a bulk copy gave up (read and
-// cleared by fast_take_wait_failure).
-__device__ unsigned g_wait_fail;
-
 // Dynamic shared memory of k_fx_round_p: the staged spectrum rows of one block (each
 // row padded by 64 bytes, so that the two rows a half-warp reads fall on different bank
 // halves), the block's phase rows, and the rows' exchange buffers.
@@ -741,6 +839,48 @@ constexpr int pow2_cols(int cap, int M) {
     return p;
 }
 template <int L> constexpr int fy_cols() { return pow2_cols(256 / fast::Split<L>::TP, L / 2); }
+// Grid of a persistent kernel: as many CTAs as fit on the GPU at once (occupancy of the
+// kernel at its shared memory), at most one per work item.
+template <typename K>
+int persistent_grid(K kern, int threads, size_t smem, int items) {
+    static const int sms = [] {
+        int dev = 0, n = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        return std::max(n, 1);
+    }();
+    if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int per = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, threads, smem) != cudaSuccess || per < 1) per = 1;
+    return std::max(1, std::min(items, per * sms));
+}
+// cuTensorMapEncodeTiled from the driver (looked up once; null when unavailable).
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static const PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess) {
+            cudaGetLastError();
+            f = nullptr;
+        }
+        return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+    }();
+    return fn;
+}
+// Tensor map of a packed spectrum for the persistent z pass: 4D array (kx: M, ky: N,
+// kz: N, slot * 3 + component) of 8-byte complex values, box of P kx by all N kz.
+bool z_tensor_map(const GridDesc& g, const float2* spec, int P, CUtensorMap* out) {
+    auto enc = tensor_map_encoder();
+    if (!enc || g.N > 256) return false;
+    const cuuint64_t dims[4] = {(cuuint64_t)g.M, (cuuint64_t)g.N, (cuuint64_t)g.N, (cuuint64_t)(3 * g.nslots)};
+    const cuuint64_t strides[3] = {(cuuint64_t)g.M * 8, (cuuint64_t)g.N * g.M * 8, (cuuint64_t)g.NNM * 8};
+    const cuuint32_t box[4] = {(cuuint32_t)P, 1, (cuuint32_t)g.N, 1};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    return enc(out, CU_TENSOR_MAP_DATA_TYPE_INT64, 4, const_cast<float2*>(spec), dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
 template <int L> constexpr int fz_cols() { return pow2_cols(128 / fast::Split<L>::TP, L / 2); }
 // x passes run 128-thread CTAs: their barriers stall fewer warps and the load phases of
 // the CTAs on an SM drift apart (x round trip 400 -> 376 us at 256^3 against 256 threads)
@@ -801,6 +941,24 @@ void launch_fzs(int mode, dim3 grid, size_t sm, cudaStream_t st, const GridDesc&
         default: launch_dyn(fast::k_fzs<L, P, Z_EQ>, grid, T, sm, st, g, mask, sp, partial); break;
     }
 }
+// The persistent z pass (plain and correction sweeps); false when it does not apply.
+template <int L, int P>
+bool launch_fz3_p(int mode, cudaStream_t st, const GridDesc& g, unsigned mask, float2* sp) {
+    if constexpr (L > 256) {
+        return false;
+    } else {
+        if (mode != Z_ITER && mode != Z_ITER_NOB) return false;
+        CUtensorMap map;
+        if (!z_tensor_map(g, sp, P, &map)) return false;
+        constexpr int T = P * fast::Split<L>::TP;
+        constexpr size_t sm = fast::ZSmem<L, P>::total;
+        auto kern = mode == Z_ITER ? fast::k_fz3_p<L, P, Z_ITER> : fast::k_fz3_p<L, P, Z_ITER_NOB>;
+        const int nper = g.N * (g.M / P);
+        const int grid = persistent_grid(kern, T, sm, nper * g.nslots);
+        kern<<<grid, T, sm, st>>>(map, g, mask, sp, nper);
+        return true;
+    }
+}
 template <int L, int P>
 void launch_fz3(int mode, dim3 grid, size_t sm, cudaStream_t st, const GridDesc& g, unsigned mask, float2* sp,
                 double* partial) {
@@ -826,7 +984,8 @@ bool fast_z_len(const GridDesc& g, int mode, unsigned mask, float2* sp, double* 
         launch_fzs<L, P>(mode, grid, sm, st, g, mask, sp, partial);
     } else {
         if (g.zvar == 1) launch_fzs<L, P>(mode, grid, sm, st, g, mask, sp, partial);
-        else launch_fz3<L, P>(mode, grid, sm, st, g, mask, sp, partial);
+        else if (!(g.zpers && launch_fz3_p<L, P>(mode, st, g, mask, sp)))
+            launch_fz3<L, P>(mode, grid, sm, st, g, mask, sp, partial);
     }
     return true;
 }
@@ -921,21 +1080,6 @@ bool chain_sweeps(const GridDesc& g) {
 }
 
 namespace {
-// Grid of a persistent kernel: as many CTAs as fit on the GPU at once (occupancy of the
-// kernel at its shared memory), at most one per work item.
-template <typename K>
-int persistent_grid(K kern, int threads, size_t smem, int items) {
-    static int sms = 0;
-    if (!sms) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    }
-    if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    int per = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, threads, smem) != cudaSuccess || per < 1) per = 1;
-    return std::max(1, std::min(items, per * std::max(sms, 1)));
-}
 template <int M, bool ADDR, bool WTAU>
 void launch_round_p(const GridDesc& g, unsigned mask, float2* sp, float* tau, const float* r32, cudaStream_t st) {
     constexpr int RW = fx_rows<M>();

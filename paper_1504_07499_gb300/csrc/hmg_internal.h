@@ -53,6 +53,9 @@ struct GridDesc {
     int nochain;           // 1: FP32 sweeps of a block are not chained through k_fx_round
     int xpers;             // 1: the chained x round trip runs as a persistent kernel that
                            //    stages its next rows with bulk copies (autotuned)
+    int zpers;             // 1: the z pass of plain and correction sweeps runs as a
+                           //    persistent kernel that stages its next columns with tiled
+                           //    tensor copies (autotuned)
     // Per-slot flags in device memory (engine launches; nullptr = use the launch's
     // mask and template modes): SF_ACTIVE, SF_ADDB (add gc E at DC, plain sweep),
     // SF_ADDR (add the defect r, correction sweep).  `resid`: this launch of the x

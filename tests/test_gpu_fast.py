@@ -158,16 +158,17 @@ def test_chained_engine_batch_is_bit_identical(ctx):
         assert list(a["iters"]) == list(b["iters"])
 
 
-@pytest.mark.parametrize("N", [64, 96, 128])
-def test_persistent_x_round_is_bit_identical(ctx, N):
+@pytest.mark.parametrize("N,pers", [(64, 8), (96, 8), (128, 8), (64, 16), (96, 16), (128, 16), (128, 24)])
+def test_persistent_kernels_are_bit_identical(ctx, N, pers):
     """Chained sweeps with the persistent x round trip (variant bit 3: bulk copies stage
-    the next row block) against the plain kernel: the same K, sweep counts and fields,
-    bit for bit, correction sweeps (r added) included."""
+    the next row block) and/or the persistent z pass (bit 4: tensor copies stage the next
+    column block) against the plain kernels: the same K, sweep counts and fields, bit for
+    bit, correction sweeps (r added) included."""
     sl = I.generate_spheres(1000, 30, 0.2)
     ph = om.voxelize(sl.spheres, 0.3, N)
     k = (0.20, 0.25, 40.0)
     out = []
-    for v in (0, 8):
+    for v in (0, pers):
         hmg.hmg_set_variant(ctx.handle, N, v)
         e = np.empty((3, 3, N, N, N))
         K, info, st = hmg.hmg_solve_fields(ctx.handle, ph, N, k, 1e-8, hmg.HMG_FP32_BULK, e)
