@@ -288,12 +288,13 @@ hmg_status hmg_solve_batch(hmg_ctx* ctx, int count, const uint8_t* const* phases
 /* Queue one solve request (copies the phase grid; returns without waiting for the
  * GPU).  A worker thread with its own CUDA stream runs the request loop: between
  * engine ticks it retires finished requests (freeing their device state) and admits
- * queued ones while their footprint (hmg_footprint) fits the context's budget, up to
- * 64 at once; every tick advances all admitted HMG_FP32_BULK requests together in one
+ * queued ones while their footprint (hmg_footprint) fits the context's budget; every
+ * tick advances all admitted HMG_FP32_BULK requests of a lane together in one
  * CUDA-graph launch (continuous batching).  HMG_FP64 requests run one at a time.
  * Grids of 192^3 voxels and more and smaller grids run in two lanes (each a worker
  * thread with its own streams and engine), so small requests do not wait for the ticks
- * of large ones and the kernels of both lanes share the GPU.
+ * of large ones and the kernels of both lanes share the GPU; the large lane runs its
+ * requests one at a time in arrival order, the small lane up to 64 at once.
  * The loop and the caller's context share one budget: the first hmg_submit on a
  * context releases the context's own solve state, and device memory that later calls
  * on the context hold counts against the loop's admissions (a request that cannot get

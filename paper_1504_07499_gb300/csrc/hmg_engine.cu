@@ -22,11 +22,12 @@ hmg_status cerr(cudaError_t e, const char* what) {
 }
 }  // namespace
 
-Engine::Engine(hmg_ctx* c, cudaStream_t s, cudaStream_t s64, bool graph) : ctx(c), st(s), st64(s64), use_graph(graph) {
+Engine::Engine(hmg_ctx* c, cudaStream_t s, cudaStream_t s64, bool graph, int priority)
+    : ctx(c), st(s), st64(s64), use_graph(graph) {
     cudaEventCreateWithFlags(&ready, cudaEventDisableTiming);
     for (int i = 0; i < kSideStreams; ++i) {
         cudaStream_t x;
-        if (cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking) == cudaSuccess) side.push_back(x);
+        if (cudaStreamCreateWithPriority(&x, cudaStreamNonBlocking, priority) == cudaSuccess) side.push_back(x);
     }
 }
 
@@ -86,6 +87,7 @@ hmg_status Engine::add(long long id, const uint8_t* phase, int N, const double k
         set_error("N = %d: need an even N = 2^a 3^b with 8 <= N <= 512", N);
         return HMG_INVALID_ARG;
     }
+    compact();   // a new entry needs a new graph: free the retired ones first
     hmg_status s = grow((int)entries.size() + 1);
     if (s != HMG_OK) return s;
     auto e = std::make_unique<Entry>();
@@ -121,15 +123,29 @@ hmg_status Engine::add(long long id, const uint8_t* phase, int N, const double k
     return cerr(cudaGetLastError(), "engine add");
 }
 
+// A removed entry is retired: its graph branch stays (its flags are 0, so its kernels
+// return at once) and its state is freed at the next compaction -- when retired entries
+// are the majority, or before an entry is added (which needs a new graph anyway) -- so the
+// graph is not rebuilt for every entry that finishes.
 void Engine::remove(Entry* e) {
+    if (e->retired) return;
+    e->retired = true;
+    ++nretired;
+    if (2 * nretired > (int)entries.size()) compact();
+}
+
+void Engine::compact() {
+    if (!nretired) return;
     cudaStreamSynchronize(st);
-    for (size_t i = 0; i < entries.size(); ++i)
-        if (entries[i].get() == e) {
-            e->st.free_all(ctx);
-            entries.erase(entries.begin() + i);
-            break;
-        }
+    cudaStreamSynchronize(st64);
+    std::vector<std::unique_ptr<Entry>> keep;
+    for (auto& up : entries) {
+        if (up->retired) up->st.free_all(ctx);
+        else keep.push_back(std::move(up));
+    }
+    entries = std::move(keep);
     for (size_t i = 0; i < entries.size(); ++i) entries[i]->index = (int)i;
+    nretired = 0;
     dirty = true;
 }
 

@@ -45,6 +45,7 @@ struct Entry {
     int rounds = 0;
     int ticks = 0;
     bool finished = false;
+    bool retired = false;   // removed by the caller; freed at the next compaction
     hmg_status result = HMG_PENDING;
     double K[9] = {0};
     hmg_info info{};
@@ -53,13 +54,17 @@ struct Entry {
 
 class Engine {
    public:
-    Engine(hmg_ctx* ctx, cudaStream_t stream, cudaStream_t stream64, bool use_graph);
+    // priority: of the engine's own streams (the CUDA stream priority; 0 is the default)
+    Engine(hmg_ctx* ctx, cudaStream_t stream, cudaStream_t stream64, bool use_graph, int priority = 0);
     ~Engine();
     // Allocate device state for one RVE and copy its phase grid (host or device).
     hmg_status add(long long id, const uint8_t* phase, int N, const double k[3], double tol, int max_iter,
                    Entry** out);
-    // Free an entry's device state (after its result has been read).
+    // Retire an entry (after its result has been read); its device state is freed at the
+    // next compaction.  The entry must not be used afterwards.
     void remove(Entry* e);
+    // Free the retired entries' state now.
+    void compact();
     // One tick for all unfinished entries.
     hmg_status tick();
     bool idle() const;
@@ -83,6 +88,7 @@ class Engine {
     int* hflags = nullptr;      // pinned
     double* hred = nullptr;     // pinned, 64 doubles per entry (the entry's residual sums)
     int cap = 0;
+    int nretired = 0;
     cudaGraphExec_t exec = nullptr;
     bool dirty = true;
     hmg_status grow(int need);

@@ -143,7 +143,10 @@ int Server::lane_of(int N) { return (long long)N * N * N >= kLargeN3 ? 0 : 1; }
 // small grids) run on their own threads, contexts and streams, so a small request's ticks
 // do not wait for a large one's and the two lanes' kernels share the GPU; they draw on one
 // budget, and a request whose state does not fit while others hold memory waits in its
-// queue.
+// queue.  The large lane runs one request at a time, in arrival order: a single 192^3 or
+// 256^3 solve already keeps HBM busy, so sharing the GPU among several would only
+// stretch each one's latency; small grids gain from running together (their kernels are
+// short and their fields partly fit the L2 cache).
 void Server::loop(int lane) {
     hmg_ctx* ctx = nullptr;
     hmg_status cs = hmg_create(&ctx, device, pool->limit);
@@ -158,6 +161,12 @@ void Server::loop(int lane) {
     bool backoff = false;
     for (;;) {
         std::vector<uint64_t> admit, fp64;
+        bool waiting;
+        {
+            std::lock_guard<std::mutex> lk(mu);
+            waiting = !queue.empty();
+        }
+        if (waiting && eng) eng->compact();   // retired requests' memory counts for admission
         {
             std::unique_lock<std::mutex> lk(mu);
             if (backoff && running.empty())   // waiting for memory another lane or the caller holds
@@ -175,7 +184,7 @@ void Server::loop(int lane) {
                     break;
                 }
                 const size_t need = state_bytes(r.N, false, 3);
-                if ((int)running.size() + (int)admit.size() >= max_slots) break;
+                if ((int)running.size() + (int)admit.size() >= lane_slots[lane]) break;
                 // the first request of an idle lane is always tried (it fits the budget
                 // alone by the check in hmg_submit); later ones while their footprint fits
                 if ((!running.empty() || !admit.empty()) && used + need > (size_t)(0.95 * (double)pool->limit)) break;

@@ -56,7 +56,7 @@ struct Server {
     hmg_status enqueue(Request&& r, uint64_t* ticket);
     int device;
     std::shared_ptr<BudgetPool> pool;
-    int max_slots = 64;
+    const int lane_slots[kLanes] = {1, 64};   // requests resident per lane at once
     std::mutex mu;
     std::condition_variable cv;
     std::deque<uint64_t> queues[kLanes];
