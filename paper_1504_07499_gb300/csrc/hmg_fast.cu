@@ -186,28 +186,29 @@ k_fz3(GridDesc g, unsigned mask, float2* __restrict__ spec, double* __restrict__
 // stages the next item's three component columns (a tiled tensor copy each: P kx by all
 // kz at one ky) in shared memory, so HBM reads overlap the arithmetic.  Plain and
 // correction sweeps only (Z_ITER, Z_ITER_NOB); same float operations as k_fz3.
+// The three components' exchanges go through one component-sized buffer in turn (a third
+// of the shared memory of k_fz3's exchange, so three CTAs fit on an SM beside the staging).
 template <int L, int P>
 struct ZSmem {
     static constexpr size_t stage_bytes = (size_t)3 * L * P * sizeof(float2);
     static constexpr size_t x_off = (stage_bytes + 127) / 128 * 128;
-    static constexpr size_t total = x_off + (size_t)3 * xslots<L>() * P * sizeof(float2);
+    static constexpr size_t total = x_off + (size_t)xslots<L>() * P * sizeof(float2);
 };
 
 template <int L, int P, int MODE>
-__global__ void __launch_bounds__(P * Split<L>::TP, 2)
+__global__ void __launch_bounds__(P * Split<L>::TP, 3)
 k_fz3_p(const __grid_constant__ CUtensorMap zmap, GridDesc g, unsigned mask, float2* __restrict__ spec, int nper) {
     constexpr int E = Split<L>::E, TP = Split<L>::TP, KPT = E / TP;
-    constexpr int NS = xslots<L>() * P;
     constexpr int N = L, M = L / 2;
     constexpr long long NNM = (long long)N * N * M;
     constexpr long long rowz = (long long)N * M;     // stride between z rows
     using Z = ZSmem<L, P>;
     extern __shared__ __align__(128) unsigned char dsm[];
-    const float2* stg = reinterpret_cast<const float2*>(dsm);   // [component][kz][column]
-    float2* sh = reinterpret_cast<float2*>(dsm + Z::x_off);      // 3 * NS
     __shared__ __align__(8) unsigned long long mbar;
     __shared__ int s_ok;
     const int p = threadIdx.x % P, t = threadIdx.x / P;
+    const float2* stg = reinterpret_cast<const float2*>(dsm);   // [component][kz][column]
+    float2* sh = reinterpret_cast<float2*>(dsm + Z::x_off) + p;  // one component at a time
     const int nkb = M / P;
     const int nitems = g.nslots * nper;
     int item = blockIdx.x;
@@ -249,10 +250,12 @@ k_fz3_p(const __grid_constant__ CUtensorMap zmap, GridDesc g, unsigned mask, flo
         while (nxt < nitems && !slot_active(g, mask, nxt / nper)) nxt += gridDim.x;
         if (threadIdx.x == 0 && nxt < nitems) issue(nxt);
 #pragma unroll
-        for (int c = 0; c < 3; ++c) stage1_write<L, true>(v[c], t, twL, sh + c * NS + p, P);
-        __syncthreads();
-#pragma unroll
-        for (int c = 0; c < 3; ++c) stage2_read<L, true>(v[c], t, sh + c * NS + p, P);
+        for (int c = 0; c < 3; ++c) {
+            stage1_write<L, true>(v[c], t, twL, sh, P);
+            __syncthreads();
+            stage2_read<L, true>(v[c], t, sh, P);
+            __syncthreads();   // the buffer takes the next component
+        }
         const bool addb = g.dflags ? (g.dflags[slot] & SF_ADDB) != 0 : MODE == Z_ITER;
         const float cE[3] = {(float)(g.gc * g.E[slot][0]), (float)(g.gc * g.E[slot][1]), (float)(g.gc * g.E[slot][2])};
 #pragma unroll
@@ -261,19 +264,19 @@ k_fz3_p(const __grid_constant__ CUtensorMap zmap, GridDesc g, unsigned mask, flo
             for (int k2 = 0; k2 < TP; ++k2)
                 green_mode_fast(kx, ky, t * KPT + i + E * k2, N, scale, ga, gb, addb, cE, v[0][i * TP + k2],
                                 v[1][i * TP + k2], v[2][i * TP + k2]);
-        __syncthreads();   // every thread has read the forward exchange
 #pragma unroll
-        for (int c = 0; c < 3; ++c) rstage2_write<L>(v[c], t, twL, sh + c * NS + p, P);
-        __syncthreads();
-#pragma unroll
-        for (int c = 0; c < 3; ++c) rstage1_read<L>(v[c], t, sh + c * NS + p, P);
+        for (int c = 0; c < 3; ++c) {
+            rstage2_write<L>(v[c], t, twL, sh, P);
+            __syncthreads();
+            rstage1_read<L>(v[c], t, sh, P);
+            __syncthreads();   // the buffer takes the next component
+        }
         float2* base = spec + (long long)slot * 3 * NNM + (long long)ky * M + kb * P + p;
 #pragma unroll
         for (int c = 0; c < 3; ++c)
 #pragma unroll
             for (int n1 = 0; n1 < E; ++n1) base[c * NNM + (long long)(TP * n1 + t) * rowz] = v[c][n1];
-        __syncthreads();   // the exchange buffer and s_ok are reused by the next item
-        item = nxt;
+        item = nxt;   // (the exchange buffer and s_ok are next written after CTA barriers)
     }
 }
 
