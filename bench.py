@@ -446,8 +446,10 @@ def main() -> None:
         K64, info64, _ = hmg.hmg_solve(ctx.handle, phase_d, N_GRID, K_PHASES, TOL, hmg.HMG_FP64)
         dt = time.perf_counter() - t
         sw = sum(info64["iters"])
+        rate = hmg.hmg_fp64_rate(ctx.handle)
         line["fp64_plain"] = {"voxel_iter_per_s": sw * N3 / dt, "solve_s": dt, "sweeps": sw,
-                              "speedup_fp32bulk_solves": dt / (ms_max / 1e3 / args.steps)}
+                              "speedup_fp32bulk_solves": dt / (ms_max / 1e3 / args.steps),
+                              "fp64_fma_rate_tflops": rate / 1e12}
         line["accuracy"]["k_err_vs_gpu_fp64"] = max(k_entry_err(Kk, K64) for Kk in Ks)
     # work-to-solution: voxel-iterations counted on the plain FP64 method's sweep count
     # (FP32 bulk runs more sweeps than FP64 to reach the same FP64 residuals)

@@ -377,6 +377,12 @@ hmg_status hmg_trace_enable(hmg_ctx* ctx, int enable);
 hmg_status hmg_trace_read(hmg_ctx* ctx, int kind, double* total_ms, long long* launches,
                           double* algo_bytes);
 
+/* Measured FP64 fused-multiply-add rate of the context's GPU (flop/s, 2 per FMA): long
+ * register-only chains over the whole device, best of five timed launches.  The plain
+ * FP64 form of the solver is bound by this rate rather than by HBM bandwidth; the
+ * paper has no counterpart (a measurement aid for the roofline of that form). */
+hmg_status hmg_fp64_rate(hmg_ctx* ctx, double* flops_out);
+
 /* Request-loop counters (zeros before the first hmg_submit): out[0] submitted,
  * out[1] completed, out[2] most requests resident on the device at once, out[3]
  * engine ticks, out[4] CUDA-graph captures, out[5] CUDA-graph launches. */

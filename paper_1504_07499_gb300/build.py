@@ -19,7 +19,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libhmg.so")
 SOURCES = ["hmg_kernels.cu", "hmg_api.cu", "hmg_capi.cu", "hmg_server.cu", "hmg_voxelize.cu",
            "hmg_noalloc.cu", "hmg_fast.cu", "hmg_engine.cu",
-           "hmg_fused.cu", "hmg_rsa.cu"]
+           "hmg_fused.cu", "hmg_rsa.cu", "hmg_peak.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-ffp-contract=off,-O2",
          "--expt-relaxed-constexpr"]

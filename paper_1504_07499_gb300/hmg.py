@@ -32,7 +32,7 @@ EXPORTS = ["hmg_version", "hmg_last_error", "hmg_create", "hmg_destroy", "hmg_vo
            "hmg_solve_batch", "hmg_submit", "hmg_poll", "hmg_footprint", "hmg_trace_enable",
            "hmg_trace_read", "hmg_equilibrium_noalloc", "hmg_set_variant", "hmg_get_variant",
            "hmg_server_stats", "hmg_solve_scheme", "hmg_solve_polarization", "hmg_rsa", "hmg_rve",
-           "hmg_submit_rve"]
+           "hmg_submit_rve", "hmg_fp64_rate"]
 HMG_NOALLOC_MAX_N = 64
 KERNEL_KINDS = ["x_forward", "y_forward", "z_green", "y_inverse", "x_inverse", "eq_x", "eq_z", "other",
                 "x_round", "fp64"]
@@ -92,6 +92,7 @@ def lib() -> C.CDLL:
         L.hmg_submit_rve.argtypes = [vp, C.c_uint64, i, d, d, i, d, d, d, d, i, C.POINTER(C.c_uint64)]
         L.hmg_equilibrium_noalloc.argtypes = [vp, i, d, d, d, vp, dp, dp]
         L.hmg_server_stats.argtypes = [vp, C.POINTER(C.c_longlong)]
+        L.hmg_fp64_rate.argtypes = [vp, dp]
         L.hmg_set_variant.argtypes = [vp, i, i]
         L.hmg_get_variant.argtypes = [vp, i, C.POINTER(C.c_int)]
         L.hmg_trace_enable.argtypes = [vp, i]
@@ -283,6 +284,13 @@ def hmg_poll(ctx: int, ticket: int):
         return st, None, None
     _check(st, (HMG_OK, HMG_NOT_CONVERGED, HMG_DIVERGED))
     return st, K.reshape(3, 3), info.as_dict()
+
+
+def hmg_fp64_rate(ctx: int) -> float:
+    """Measured FP64 FMA rate of the context's GPU (flop/s)."""
+    r = np.zeros(1)
+    _check(lib().hmg_fp64_rate(ctx, _dbuf(r)))
+    return float(r[0])
 
 
 def hmg_server_stats(ctx: int) -> dict:

@@ -216,3 +216,10 @@ def test_device_resident_phase(ctx):
     K1, _, _ = ctx.solve(ph, K3, 1e-8, hmg.HMG_FP64)
     K2, _, _ = hmg.hmg_solve(ctx.handle, d, N, K3, 1e-8, hmg.HMG_FP64)
     assert np.array_equal(K1, K2)   # same inputs, same launch order: bitwise identical
+
+
+def test_fp64_rate_is_measured(ctx):
+    """The FP64 FMA-rate probe behind the FP64 form's roofline returns a finite rate in
+    the range of any current GPU (0.1 to 100 TFLOP/s)."""
+    r = hmg.hmg_fp64_rate(ctx.handle)
+    assert 1e11 < r < 1e14
