@@ -47,6 +47,15 @@ typedef struct {
     double cx, cy, cz, r;
 } hmg_sphere;
 
+/* One coated cylinder (§6 outlook: RVEs with cylinders, or spheres and cylinders):
+ * centre in the periodic unit cube, unit axis (ux, uy, uz), OUTER radius r and OUTER
+ * length h (coating included).  The coating has the same thickness l r on the lateral
+ * surface and on the flat ends: the core has radius (1 - l) r and length h - 2 l r.
+ * A cylinder of length at least 1 + 2 l r along a grid axis is a continuous fiber. */
+typedef struct {
+    double cx, cy, cz, ux, uy, uz, r, h;
+} hmg_cylinder;
+
 typedef enum {
     HMG_OK = 0,
     HMG_PENDING = 1,          /* hmg_poll: request not finished yet */
@@ -133,6 +142,23 @@ hmg_status hmg_destroy(hmg_ctx* ctx);
  * do not overlap). */
 hmg_status hmg_voxelize(hmg_ctx* ctx, const hmg_sphere* spheres, size_t n, double layer,
                         int N, uint8_t* phase_out);
+
+/* hmg_voxelize for coated spheres and coated cylinders together (§6 outlook).  The
+ * spheres follow the rule of hmg_voxelize; the cylinders the integer rule: coordinates in
+ * units of 1 / (2 N 256) (voxel centres at odd multiples of 256), a centre c mapped as a
+ * sphere's, the axis to A = floor(1024 u + 1/2) per component, squared radii
+ * floor((r S)^2 + 1/2) and floor(((1-l) r S)^2 + 1/2), half-lengths floor((h/2) S + 1/2) and
+ * floor((h/2 - l r) S + 1/2) (S = 2 N 256); with d the signed minimum-image offset of a
+ * voxel centre from the centre (components in [-S/2, S/2)) and t = d . A, the voxel lies in
+ * the cylinder when |d|^2 |A|^2 - t^2 <= R^2 |A|^2 and t^2 <= H^2 |A|^2 (int64).  A voxel is
+ * inclusion inside any core (sphere or cylinder), else coating inside any outer shape, else
+ * matrix.  Either count may be 0 (not both); spheres and cylinders: host or device.
+ * Overlaps are checked between spheres only (the generator keeps cylinders apart).
+ * Errors: HMG_INVALID_ARG as hmg_voxelize, and for a cylinder with a non-finite value,
+ * r outside (0, 0.5), h outside (0, 2] or an axis of length other than 1. */
+hmg_status hmg_voxelize_mixed(hmg_ctx* ctx, const hmg_sphere* spheres, size_t n_spheres,
+                              const hmg_cylinder* cylinders, size_t n_cylinders, double layer, int N,
+                              uint8_t* phase_out);
 
 /* Seeded placement of n identical, non-overlapping spheres of outer radius r in the
  * periodic unit cube, computed on the GPU (§2: the RVEs come from random sequential

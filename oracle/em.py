@@ -119,6 +119,80 @@ def voxelize(spheres, layer: float, N: int) -> np.ndarray:
     return phase
 
 
+# Coated cylinders (§6: RVEs "with cylinders or both spheres and cylinders").  A cylinder
+# has a centre, a unit axis u, an outer radius r and an outer length h; the coating has the
+# same thickness l r on the lateral surface and on the flat ends, so the core has radius
+# (1 - l) r and length h - 2 l r.  Integer rule (coordinates in units of 1 / (2 N GC),
+# voxel centres at odd multiples of GC): the centre maps like a sphere's; the axis to
+# A = floor(u 1024 + 1/2) per component; squared radii to floor((r S)^2 + 1/2) and
+# floor(((1 - l) r S)^2 + 1/2); half-lengths to floor((h/2) S + 1/2) and
+# floor((h/2 - l r) S + 1/2).  With d the signed minimum-image offset of a voxel centre
+# from the cylinder centre (each component in [-S/2, S/2)) and t = d . A, the voxel lies in
+# the cylinder when |d|^2 |A|^2 - t^2 <= R^2 |A|^2 (radial) and t^2 <= H^2 |A|^2 (axial),
+# in int64 (the quantization keeps every product below 2^63 up to N = 512).
+
+QUANT_GC = 256
+AXIS_Q = 1024
+
+
+def quantize_cylinders(cylinders, layer: float, N: int):
+    """Integer cylinder data: (n, 10) rows (Cx, Cy, Cz, Ax, Ay, Az, R_out^2, R_in^2, H_out,
+    H_in), and S."""
+    S = 2 * N * QUANT_GC
+    out = []
+    for cx, cy, cz, ux, uy, uz, r, h in np.asarray(cylinders, dtype=np.float64).reshape(-1, 8):
+        cen = []
+        for c in (cx, cy, cz):
+            cw = c - math.floor(c)
+            cen.append(math.floor(cw * S + 0.5) % S)
+        ax = [math.floor(u * AXIS_Q + 0.5) for u in (ux, uy, uz)]
+        t_out = r * S
+        t_in = (1.0 - layer) * r * S
+        out.append((*cen, *ax, math.floor(t_out * t_out + 0.5), math.floor(t_in * t_in + 0.5),
+                    math.floor(0.5 * h * S + 0.5), math.floor((0.5 * h - layer * r) * S + 0.5)))
+    return np.array(out, dtype=np.int64).reshape(-1, 10), S
+
+
+def cylinder_masks(cylinders, layer: float, N: int):
+    """(core, outer) boolean grids (z, y, x) of the coated cylinders."""
+    q, S = quantize_cylinders(cylinders, layer, N)
+    v = (2 * np.arange(N, dtype=np.int64) + 1) * QUANT_GC
+    core = np.zeros((N, N, N), dtype=bool)
+    outer = np.zeros((N, N, N), dtype=bool)
+    for cx, cy, cz, ax, ay, az, ro2, ri2, ho, hi in q:
+        d = []
+        for c in (cx, cy, cz):
+            d.append((v - c + S // 2) % S - S // 2)          # signed minimum image
+        dx, dy, dz = d[0][None, None, :], d[1][None, :, None], d[2][:, None, None]
+        a2 = ax * ax + ay * ay + az * az
+        t = dx * ax + dy * ay + dz * az
+        rad = (dx * dx + dy * dy + dz * dz) * a2 - t * t
+        t2 = t * t
+        outer |= (rad <= ro2 * a2) & (t2 <= ho * ho * a2)
+        if hi > 0:
+            core |= (rad <= ri2 * a2) & (t2 <= hi * hi * a2)
+    return core, outer
+
+
+def voxelize_mixed(spheres, cylinders, layer: float, N: int) -> np.ndarray:
+    """Three-phase grid of coated spheres and coated cylinders (same layer l): inclusion
+    inside any core, else coating inside any outer shape, else matrix."""
+    phase = np.zeros((N, N, N), dtype=np.uint8)
+    incl = np.zeros((N, N, N), dtype=bool)
+    coat = np.zeros((N, N, N), dtype=bool)
+    if spheres is not None and len(spheres):
+        ph_s = voxelize(spheres, layer, N)
+        incl |= ph_s == INCLUSION
+        coat |= ph_s != MATRIX
+    if cylinders is not None and len(cylinders):
+        core, outer = cylinder_masks(cylinders, layer, N)
+        incl |= core
+        coat |= outer
+    phase[coat] = COATING
+    phase[incl] = INCLUSION
+    return phase
+
+
 def coating_fraction(layer: float, f_sp: float) -> float:
     """Coating volume fraction of spheres of total fraction f_sp (§5, Table 0)."""
     return (1.0 - (1.0 - layer) ** 3) * f_sp

@@ -198,13 +198,15 @@ hmg_status hmg_trace_read(hmg_ctx* ctx, int kind, double* total_ms, long long* l
     return HMG_OK;
 }
 
-hmg_status hmg_voxelize(hmg_ctx* ctx, const hmg_sphere* spheres, size_t n, double layer, int N,
-                        uint8_t* phase_out) {
-    g_last_error.clear();
+namespace {
+// Spheres and cylinders into a three-phase grid: host validation and quantization, the
+// sphere kernel (or zeros), then the cylinder kernel merging into the same grid.
+hmg_status voxelize_impl(hmg_ctx* ctx, const hmg_sphere* spheres, size_t n, const hmg_cylinder* cylinders,
+                         size_t nc, double layer, int N, uint8_t* phase_out) {
     hmg_status st = check_common(ctx, N, phase_out);
     if (st != HMG_OK) return st;
-    if (!spheres || n == 0 || n > 100000) {
-        set_error("need 1..100000 spheres");
+    if ((n && !spheres) || (nc && !cylinders) || n + nc == 0 || n > 100000 || nc > 100000) {
+        set_error("need 1..100000 spheres or cylinders");
         return HMG_INVALID_ARG;
     }
     if (!(layer > 0.0 && layer < 1.0)) {
@@ -213,17 +215,40 @@ hmg_status hmg_voxelize(hmg_ctx* ctx, const hmg_sphere* spheres, size_t n, doubl
     }
     DeviceGuard dg(ctx->device);
     std::vector<hmg_sphere> h(n);
-    if (is_device_ptr(spheres)) {
-        st = cuda_status(cudaMemcpy(h.data(), spheres, n * sizeof(hmg_sphere), cudaMemcpyDeviceToHost), "sphere copy");
-        if (st != HMG_OK) return st;
-    } else {
-        memcpy(h.data(), spheres, n * sizeof(hmg_sphere));
+    std::vector<hmg_cylinder> hc(nc);
+    if (n) {
+        if (is_device_ptr(spheres)) {
+            st = cuda_status(cudaMemcpy(h.data(), spheres, n * sizeof(hmg_sphere), cudaMemcpyDeviceToHost), "sphere copy");
+            if (st != HMG_OK) return st;
+        } else {
+            memcpy(h.data(), spheres, n * sizeof(hmg_sphere));
+        }
+    }
+    if (nc) {
+        if (is_device_ptr(cylinders)) {
+            st = cuda_status(cudaMemcpy(hc.data(), cylinders, nc * sizeof(hmg_cylinder), cudaMemcpyDeviceToHost),
+                             "cylinder copy");
+            if (st != HMG_OK) return st;
+        } else {
+            memcpy(hc.data(), cylinders, nc * sizeof(hmg_cylinder));
+        }
     }
     for (size_t i = 0; i < n; ++i) {
         const hmg_sphere& s = h[i];
         if (!(std::isfinite(s.cx) && std::isfinite(s.cy) && std::isfinite(s.cz) && std::isfinite(s.r)) ||
             !(s.r > 0.0 && s.r < 0.5)) {
             set_error("sphere %zu: non-finite value or radius outside (0, 0.5)", i);
+            return HMG_INVALID_ARG;
+        }
+    }
+    for (size_t i = 0; i < nc; ++i) {
+        const hmg_cylinder& c = hc[i];
+        const double u2 = c.ux * c.ux + c.uy * c.uy + c.uz * c.uz;
+        if (!(std::isfinite(c.cx) && std::isfinite(c.cy) && std::isfinite(c.cz) && std::isfinite(u2) &&
+              std::isfinite(c.r) && std::isfinite(c.h)) ||
+            !(c.r > 0.0 && c.r < 0.5) || !(c.h > 0.0 && c.h <= 2.0) || !(std::fabs(u2 - 1.0) <= 1e-6)) {
+            set_error("cylinder %zu: non-finite value, radius outside (0, 0.5), length outside (0, 2] or "
+                      "axis not of unit length", i);
             return HMG_INVALID_ARG;
         }
     }
@@ -261,27 +286,67 @@ hmg_status hmg_voxelize(hmg_ctx* ctx, const hmg_sphere* spheres, size_t n, doubl
         q[5 * i + 3] = (long long)std::floor(t_out * t_out + 0.5);
         q[5 * i + 4] = (long long)std::floor(t_in * t_in + 0.5);
     }
+    const long long Sc = 2LL * N * 256;
+    const double Scd = (double)Sc;
+    std::vector<long long> qc(10 * nc);
+    for (size_t i = 0; i < nc; ++i) {
+        const hmg_cylinder& c = hc[i];
+        const double c3[3] = {c.cx, c.cy, c.cz}, u3[3] = {c.ux, c.uy, c.uz};
+        for (int a = 0; a < 3; ++a) {
+            const double cw = c3[a] - std::floor(c3[a]);
+            qc[10 * i + a] = ((long long)std::floor(cw * Scd + 0.5)) % Sc;
+            qc[10 * i + 3 + a] = (long long)std::floor(u3[a] * 1024.0 + 0.5);
+        }
+        const double t_out = c.r * Scd;
+        const double t_in = (1.0 - layer) * c.r * Scd;
+        qc[10 * i + 6] = (long long)std::floor(t_out * t_out + 0.5);
+        qc[10 * i + 7] = (long long)std::floor(t_in * t_in + 0.5);
+        qc[10 * i + 8] = (long long)std::floor(0.5 * c.h * Scd + 0.5);
+        qc[10 * i + 9] = (long long)std::floor((0.5 * c.h - layer * c.r) * Scd + 0.5);
+    }
     long long* qd = nullptr;
     uint8_t* tmp = nullptr;
     const size_t N3 = (size_t)N * N * N;
     const bool dev_out = is_device_ptr(phase_out);
-    if (cudaMalloc(&qd, q.size() * sizeof(long long)) != cudaSuccess ||
-        (!dev_out && cudaMalloc(&tmp, N3) != cudaSuccess)) {
+    const size_t qbytes = (q.size() + qc.size()) * sizeof(long long);
+    if (cudaMalloc(&qd, qbytes) != cudaSuccess || (!dev_out && cudaMalloc(&tmp, N3) != cudaSuccess)) {
         cudaGetLastError();
         if (qd) cudaFree(qd);
         set_error("cannot allocate voxelization buffers");
         return HMG_OUT_OF_MEMORY;
     }
-    cudaMemcpyAsync(qd, q.data(), q.size() * sizeof(long long), cudaMemcpyHostToDevice, ctx->stream);
+    if (!q.empty()) cudaMemcpyAsync(qd, q.data(), q.size() * sizeof(long long), cudaMemcpyHostToDevice, ctx->stream);
+    if (!qc.empty())
+        cudaMemcpyAsync(qd + q.size(), qc.data(), qc.size() * sizeof(long long), cudaMemcpyHostToDevice, ctx->stream);
     uint8_t* dst = dev_out ? phase_out : tmp;
     const int ev = ctx->tracer.on ? ctx->tracer.begin(ctx->stream) : -1;
-    launch_voxelize(qd, (int)n, N, S, dst, ctx->stream);
+    if (n) launch_voxelize(qd, (int)n, N, S, dst, ctx->stream);
+    else cudaMemsetAsync(dst, 0, N3, ctx->stream);
+    if (nc) launch_voxelize_cyl(qd + q.size(), (int)nc, N, Sc, dst, ctx->stream);
     if (ev >= 0) ctx->tracer.end(ev, HMG_K_OTHER, (double)N3, ctx->stream);
     if (!dev_out) cudaMemcpyAsync(phase_out, tmp, N3, cudaMemcpyDeviceToHost, ctx->stream);
     st = check_launch(ctx, "voxelize");
     cudaFree(qd);
     if (tmp) cudaFree(tmp);
     return st;
+}
+}  // namespace
+
+hmg_status hmg_voxelize(hmg_ctx* ctx, const hmg_sphere* spheres, size_t n, double layer, int N,
+                        uint8_t* phase_out) {
+    g_last_error.clear();
+    if (n == 0) {
+        set_error("need 1..100000 spheres");
+        return HMG_INVALID_ARG;
+    }
+    return voxelize_impl(ctx, spheres, n, nullptr, 0, layer, N, phase_out);
+}
+
+hmg_status hmg_voxelize_mixed(hmg_ctx* ctx, const hmg_sphere* spheres, size_t n_spheres,
+                              const hmg_cylinder* cylinders, size_t n_cylinders, double layer, int N,
+                              uint8_t* phase_out) {
+    g_last_error.clear();
+    return voxelize_impl(ctx, spheres, n_spheres, cylinders, n_cylinders, layer, N, phase_out);
 }
 
 namespace {

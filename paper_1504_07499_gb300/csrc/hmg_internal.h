@@ -166,5 +166,7 @@ void launch_convert_back(const R* src, double* dst, long long n, cudaStream_t st
 
 // Voxelization (hmg_voxelize.cu): q holds n quantized spheres (cx, cy, cz, R_out^2, R_in^2).
 void launch_voxelize(const long long* q, int n, int N, long long S, uint8_t* out, cudaStream_t st);
+// Coated cylinders merged into a phase grid (q: 10 integers per cylinder, GC = 256 units).
+void launch_voxelize_cyl(const long long* q, int n, int N, long long S, uint8_t* out, cudaStream_t st);
 
 }  // namespace hmg

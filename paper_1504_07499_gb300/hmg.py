@@ -32,7 +32,7 @@ EXPORTS = ["hmg_version", "hmg_last_error", "hmg_create", "hmg_destroy", "hmg_vo
            "hmg_solve_batch", "hmg_submit", "hmg_poll", "hmg_footprint", "hmg_trace_enable",
            "hmg_trace_read", "hmg_equilibrium_noalloc", "hmg_set_variant", "hmg_get_variant",
            "hmg_server_stats", "hmg_solve_scheme", "hmg_solve_polarization", "hmg_rsa", "hmg_rve",
-           "hmg_submit_rve", "hmg_fp64_rate"]
+           "hmg_submit_rve", "hmg_fp64_rate", "hmg_voxelize_mixed"]
 HMG_NOALLOC_MAX_N = 64
 KERNEL_KINDS = ["x_forward", "y_forward", "z_green", "y_inverse", "x_inverse", "eq_x", "eq_z", "other",
                 "x_round", "fp64"]
@@ -76,6 +76,7 @@ def lib() -> C.CDLL:
         L.hmg_create.argtypes = [C.POINTER(vp), i, sz]
         L.hmg_destroy.argtypes = [vp]
         L.hmg_voxelize.argtypes = [vp, vp, sz, d, i, vp]
+        L.hmg_voxelize_mixed.argtypes = [vp, vp, sz, vp, sz, d, i, vp]
         L.hmg_rsa.argtypes = [vp, C.c_uint64, i, d, C.c_longlong, vp, C.POINTER(i)]
         L.hmg_rve.argtypes = [vp, C.c_uint64, i, d, C.c_longlong, d, i, vp, vp, C.POINTER(i)]
         L.hmg_solve.argtypes = [vp, vp, i, d, d, d, d, i, i, dp, C.POINTER(hmg_info)]
@@ -157,6 +158,15 @@ def hmg_voxelize(ctx: int, spheres, layer: float, N: int, phase_out) -> None:
     """spheres: (n, 4) float64 array (cx, cy, cz, r) or device tensor; phase_out: N^3 uint8."""
     n = spheres.shape[0]
     _check(lib().hmg_voxelize(ctx, _ptr(spheres), n, layer, N, _ptr(phase_out)))
+
+
+def hmg_voxelize_mixed(ctx: int, spheres, cylinders, layer: float, N: int, phase_out) -> None:
+    """spheres: (n, 4) (or None), cylinders: (m, 8) cx, cy, cz, ux, uy, uz, r, h (or None);
+    host arrays or device tensors; phase_out: N^3 uint8."""
+    ns = 0 if spheres is None else spheres.shape[0]
+    nc = 0 if cylinders is None else cylinders.shape[0]
+    _check(lib().hmg_voxelize_mixed(ctx, _ptr(spheres) if ns else None, ns, _ptr(cylinders) if nc else None, nc,
+                                    layer, N, _ptr(phase_out)))
 
 
 def hmg_rsa(ctx: int, seed: int, n: int, r: float, max_candidates: int = 400_000, spheres_out=None):

@@ -185,6 +185,93 @@ def generate_spheres(seed: int, n: int, f: float, max_candidates: int = 400_000)
     return SphereList(sph, gen, seed, n, f)
 
 
+def random_axis(u1: float, u2: float) -> np.ndarray:
+    """Unit vector uniform on the sphere from two uniforms (z = 2 u1 - 1, azimuth 2 pi u2)."""
+    z = 2.0 * u1 - 1.0
+    s = math.sqrt(max(0.0, 1.0 - z * z))
+    phi = 2.0 * math.pi * u2
+    return np.array([s * math.cos(phi), s * math.sin(phi), z])
+
+
+def _segment_distance_sq(w: np.ndarray, a: np.ndarray, b: np.ndarray) -> float:
+    """Smallest squared distance between the segments s a (s in [-1, 1]) and w + t b
+    (t in [-1, 1]): the minimum of the convex quadratic |s a - t b - w|^2 over the square,
+    inside it or on one of its four edges."""
+    aa, bb, ab = float(a @ a), float(b @ b), float(a @ b)
+    aw, bw = float(a @ w), float(b @ w)
+
+    def f(s, t):
+        d = s * a - t * b - w
+        return float(d @ d)
+
+    def clamp(x):
+        return min(1.0, max(-1.0, x))
+
+    best = math.inf
+    det = aa * bb - ab * ab
+    if det > 1e-14 * max(aa * bb, 1e-300):
+        s = (aw * bb - ab * bw) / det
+        t = (ab * aw - aa * bw) / det
+        if -1.0 <= s <= 1.0 and -1.0 <= t <= 1.0:
+            return f(s, t)
+    for s in (-1.0, 1.0):   # edges s = +-1: t minimizes |s a - w - t b|^2
+        t = clamp((s * ab - bw) / bb) if bb > 0 else 0.0
+        best = min(best, f(s, t))
+    for t in (-1.0, 1.0):
+        s = clamp((t * ab + aw) / aa) if aa > 0 else 0.0
+        best = min(best, f(s, t))
+    return best
+
+
+def generate_cylinders(seed: int, n: int, r: float, h: float, axis=None, spheres: int = 0, r_sphere: float = 0.0,
+                       max_candidates: int = 400_000):
+    """Seeded RSA of ``n`` coated cylinders (outer radius r, outer length h) and
+    ``spheres`` spheres of radius r_sphere in the periodic unit cube (§6: RVEs with
+    cylinders, or spheres and cylinders).  Cylinders come first, then spheres; a
+    candidate is accepted when its capsule (its axis segment of half-length h/2 inflated
+    by its radius; a sphere is a point inflated by its radius) keeps clear of every
+    accepted object's capsule; a flat-ended cylinder lies inside its capsule, so the
+    objects never overlap.
+    Each cylinder candidate draws 5 uniforms (centre, then the axis unless ``axis`` fixes
+    it), each sphere candidate 3.  Needs h/2 + r <= 1/4 (one periodic image per pair).
+    Returns (spheres (k, 4), cylinders (n, 8): cx, cy, cz, ux, uy, uz, r, h)."""
+    if not (0.5 * h + max(r, r_sphere) <= 0.25 + 1e-12):
+        raise ValueError("objects must fit a quarter of the cell (h/2 + r <= 1/4)")
+    rng = SplitMix64(seed, 5)
+    objs = []   # (centre, half-axis vector, radius)
+    cyl, sph = [], []
+    used = 0
+    fixed = None if axis is None else np.asarray(axis, dtype=np.float64) / np.linalg.norm(axis)
+    while (len(cyl) < n or len(sph) < spheres) and used < max_candidates:
+        is_cyl = len(cyl) < n
+        u = rng.uniform(5 if is_cyl else 3)
+        used += 1
+        c = u[:3]
+        if is_cyl:
+            ax = fixed if fixed is not None else random_axis(u[3], u[4])
+            half, rad = 0.5 * h * ax, r
+        else:
+            ax = np.zeros(3)
+            half, rad = np.zeros(3), r_sphere
+        ok = True
+        for c2, h2, r2 in objs:
+            w = c2 - c
+            w = w - np.floor(w + 0.5)                      # minimum image of the centre offset
+            if _segment_distance_sq(w, half, h2) <= (rad + r2) * (rad + r2):
+                ok = False
+                break
+        if not ok:
+            continue
+        objs.append((c, half, rad))
+        if is_cyl:
+            cyl.append([c[0], c[1], c[2], ax[0], ax[1], ax[2], r, h])
+        else:
+            sph.append([c[0], c[1], c[2], r_sphere])
+    if len(cyl) < n or len(sph) < spheres:
+        raise RuntimeError("RSA of cylinders and spheres did not place every object")
+    return np.array(sph).reshape(-1, 4), np.array(cyl).reshape(-1, 8)
+
+
 def centred_sphere(r: float = 0.25) -> np.ndarray:
     """One sphere centred at (0.5, 0.5, 0.5): a voxel corner for every even N."""
     return np.array([[0.5, 0.5, 0.5, r]])
