@@ -370,7 +370,11 @@ hmg_status hmg_poll(hmg_ctx* ctx, uint64_t ticket, double K_out[9], hmg_info* in
  *          256; bit-identical results).
  * The autotuner chooses bits 0, 1, 3 and 4 and leaves bit 2 clear.  hmg_set_variant pins
  * `variant` (0 .. 31) for size N, or clears the choice (-1) so that the next solve
- * times them again.  All give the same results to rounding. */
+ * times them again.  All give the same results to rounding.
+ * When the environment variable HMG_TUNE_CACHE names a file, a context takes the choice
+ * recorded there for its GPU (device name and SM count) and N instead of timing, and
+ * appends the choices it times, one line "<device name>|<SM count>|<N>|<variant>" each
+ * (the last line for a key wins). */
 hmg_status hmg_set_variant(hmg_ctx* ctx, int N, int variant);
 
 /* The variant chosen for size N (-1 if none yet). */

@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <functional>
 #include <map>
@@ -203,10 +204,66 @@ static float time_launches(cudaStream_t st, const std::function<void()>& f, int 
     return ms;
 }
 
+// On-disk record of the autotuner's choices, opt-in through the environment variable
+// HMG_TUNE_CACHE (a file path): one line "<device name>|<SM count>|<N>|<variant>" per
+// choice, the last line for a key wins.  A context takes a recorded choice for its GPU
+// instead of timing the variants, and appends what it times.
+namespace {
+std::mutex g_tune_mu;
+
+std::string tune_key(int device, int N) {
+    cudaDeviceProp p;
+    if (cudaGetDeviceProperties(&p, device) != cudaSuccess) {
+        cudaGetLastError();
+        return std::string();
+    }
+    return std::string(p.name) + "|" + std::to_string(p.multiProcessorCount) + "|" + std::to_string(N) + "|";
+}
+
+bool tune_cache_read(int device, int N, int* variant) {
+    const char* path = std::getenv("HMG_TUNE_CACHE");
+    if (!path || !*path) return false;
+    const std::string key = tune_key(device, N);
+    if (key.empty()) return false;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    FILE* f = std::fopen(path, "r");
+    if (!f) return false;
+    char line[512];
+    bool found = false;
+    while (std::fgets(line, sizeof line, f)) {
+        const std::string l(line);
+        if (l.compare(0, key.size(), key) != 0) continue;
+        const int v = std::atoi(l.c_str() + key.size());
+        if (v >= 0 && v < 32 && !(v & 4)) {
+            *variant = v;
+            found = true;
+        }
+    }
+    std::fclose(f);
+    return found;
+}
+
+void tune_cache_write(int device, int N, int variant) {
+    const char* path = std::getenv("HMG_TUNE_CACHE");
+    if (!path || !*path) return;
+    const std::string key = tune_key(device, N);
+    if (key.empty()) return;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    if (FILE* f = std::fopen(path, "a")) {
+        std::fprintf(f, "%s%d\n", key.c_str(), variant);
+        std::fclose(f);
+    }
+}
+}  // namespace
+
 int autotune_z(::hmg_ctx* c, GridDesc g, SolveState* s, cudaStream_t st) {
     auto it = c->ztune.find(g.N);
     if (it != c->ztune.end()) return it->second;
     int best = 0;
+    if (tune_cache_read(c->device, g.N, &best)) {
+        c->ztune[g.N] = best;
+        return best;
+    }
     if (!s->spec32 || !s->f32buf) {
         c->ztune[g.N] = best;
         return best;
@@ -269,6 +326,7 @@ int autotune_z(::hmg_ctx* c, GridDesc g, SolveState* s, cudaStream_t st) {
     cudaGetLastError();
     best = zbest | (xybest << 1) | (xpbest << 3) | (zpbest << 4);
     c->ztune[g.N] = best;
+    tune_cache_write(c->device, g.N, best);
     return best;
 }
 

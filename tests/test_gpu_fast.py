@@ -180,3 +180,35 @@ def test_persistent_kernels_are_bit_identical(ctx, N, pers):
     assert np.array_equal(out[0][0], out[1][0])
     assert list(out[0][1]["iters"]) == list(out[1][1]["iters"])
     assert np.array_equal(out[0][2], out[1][2])
+
+
+def test_autotuner_choices_persist_on_disk(tmp_path):
+    """With HMG_TUNE_CACHE set, a fresh process records the variant it times, and a later
+    process takes the recorded choice (here overwritten with another valid one) instead of
+    timing."""
+    import os
+    import subprocess
+    import sys
+    from conftest import ROOT
+    cache = tmp_path / "variants"
+    prog = (
+        "import sys, numpy as np; sys.path.insert(0, sys.argv[1])\n"
+        "from paper_1504_07499_gb300 import hmg, inputs as I\n"
+        "c = hmg.Context(0)\n"
+        "ph = I.random_phase_grid(3, 64)\n"
+        "e = np.zeros((3, 64, 64, 64)); e[0] = 1.0\n"
+        "hmg.hmg_solve(c.handle, ph, 64, I.K_PHASES, 1e-8, hmg.HMG_FP32_BULK, max_iter=8,"
+        " allow=(hmg.HMG_NOT_CONVERGED,))\n"
+        "print(hmg.hmg_get_variant(c.handle, 64))\n")
+    env = dict(os.environ, HMG_TUNE_CACHE=str(cache))
+    r = subprocess.run([sys.executable, "-c", prog, ROOT], env=env, capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stderr[-2000:]
+    first = int(r.stdout.split()[-1])
+    lines = cache.read_text().splitlines()
+    assert len(lines) == 1 and lines[0].endswith(f"|64|{first}")
+    other = 17 if first != 17 else 1
+    cache.write_text(lines[0].rsplit("|", 1)[0] + f"|{other}\n")
+    r = subprocess.run([sys.executable, "-c", prog, ROOT], env=env, capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stderr[-2000:]
+    assert int(r.stdout.split()[-1]) == other
+    assert len(cache.read_text().splitlines()) == 1          # nothing timed, nothing appended
