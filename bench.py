@@ -232,7 +232,7 @@ def main() -> None:
                          "layers: the paper's sweep over the coating layer at 64^3/128^3/256^3")
     ap.add_argument("--requests", type=int, default=48, help="serve mode: requests per arrival rate")
     ap.add_argument("--variant", type=int, default=-1,
-                    help="pin the FP32 kernel variant of the 256^3 grid (0..7, see hmg_set_variant); "
+                    help="pin the FP32 kernel variant of the 256^3 grid (0..63, see hmg_set_variant); "
                          "default: autotuned on the device")
     ap.add_argument("--grid", type=int, default=256, choices=[256, 512],
                     help="single mode: grid size of the RVE (256 is the benchmark workload; 512 the "

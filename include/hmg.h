@@ -368,8 +368,12 @@ hmg_status hmg_poll(hmg_ctx* ctx, uint64_t ticket, double K_out[9], hmg_info* in
  *          persistent kernel whose CTAs stage the next column block (three tiled tensor
  *          copies) in shared memory while they transform the current one (sizes up to
  *          256; bit-identical results).
- * The autotuner chooses bits 0, 1, 3 and 4 and leaves bit 2 clear.  hmg_set_variant pins
- * `variant` (0 .. 31) for size N, or clears the choice (-1) so that the next solve
+ *   bit 5: with chained sweeps (sizes 64, 128, 192, 256), the y inverse of one sweep, the
+ *          x round trip and the y forward of the next sweep run as one persistent kernel
+ *          whose CTAs take whole (component, z) planes, so that each plane stays in L2
+ *          between the three passes (bit-identical results; bit 3 then has no effect).
+ * The autotuner chooses bits 0, 1, 3, 4 and 5 and leaves bit 2 clear.  hmg_set_variant pins
+ * `variant` (0 .. 63) for size N, or clears the choice (-1) so that the next solve
  * times them again.  All give the same results to rounding.
  * When the environment variable HMG_TUNE_CACHE names a file, a context takes the choice
  * recorded there for its GPU (device name and SM count) and N instead of timing, and
@@ -395,7 +399,9 @@ typedef enum {
     HMG_K_X_ROUND = 8,     /* x pass inverse + update of one sweep fused with the
                               polarization + x pass forward of the next (steps 5-7, 2-3) */
     HMG_K_FP64 = 9,        /* every pass of an FP64 sweep or FP64 equilibrium test */
-    HMG_K_COUNT = 10
+    HMG_K_YXY = 10,        /* y pass inverse + x round trip + y pass forward of the next sweep,
+                              one persistent kernel over (component, z) planes (steps 5-7, 2-3) */
+    HMG_K_COUNT = 11
 } hmg_kernel_kind;
 
 /* Start (enable = 1, counters reset) or stop (0) timing every kernel the solver

@@ -323,8 +323,27 @@ int autotune_z(::hmg_ctx* c, GridDesc g, SolveState* s, cudaStream_t st) {
         xpbest = xms[1] < xms[0] ? 1 : 0;
         if (fast_take_wait_failure()) xpbest = 0;
     }
+    // y inverse + x round trip + y forward: separate passes or the plane kernel
+    int yxybest = 0;
+    g.xpers = xpbest;
+    if (chain_sweeps(g) && fast_yxy_available(g)) {
+        float yms[2];
+        for (int v = 0; v < 2; ++v) {
+            yms[v] = time_launches(st, [&] {
+                if (v == 1) {
+                    fast_yxy(g, false, false, all, s->spec32, s->f32buf, nullptr, st);
+                    return;
+                }
+                launch_y_pass<float>(g, false, all, s->spec32, st);
+                fast_x_round(g, false, false, all, s->spec32, s->f32buf, nullptr, st);
+                launch_y_pass<float>(g, true, all, s->spec32, st);
+            }, 4);
+        }
+        yxybest = yms[1] < yms[0] ? 1 : 0;
+        if (fast_take_wait_failure()) yxybest = 0;
+    }
     cudaGetLastError();
-    best = zbest | (xybest << 1) | (xpbest << 3) | (zpbest << 4);
+    best = zbest | (xybest << 1) | (xpbest << 3) | (zpbest << 4) | (yxybest << 5);
     c->ztune[g.N] = best;
     tune_cache_write(c->device, g.N, best);
     return best;
@@ -554,18 +573,26 @@ void Solver::block_sweep(unsigned mask, int b, int blk, int zmode, bool addr, co
     const double f = (double)popc(mask) * 3.0 * (double)g.N3;   // field elements moved per array
     const double F = sizeof(float);
     double* pb = psweep ? psweep : s->partial;
+    // with the plane kernel, the y forward of sweeps after the first was done by the
+    // previous sweep's plane kernel
+    const bool yxy = g.yxy && fast_yxy_available(g);
     if (b == 0)
         HMG_TRACED(HMG_K_X_FORWARD, f * 2 * F + (double)g.N3,
                    launch_x_forward<float>(g, XF_POLARIZE, mask, s->f32buf, s->spec32, nullptr, st));
-    HMG_TRACED(HMG_K_Y_FORWARD, f * 2 * F, launch_y_pass<float>(g, true, mask, s->spec32, st));
+    if (b == 0 || !yxy) HMG_TRACED(HMG_K_Y_FORWARD, f * 2 * F, launch_y_pass<float>(g, true, mask, s->spec32, st));
     HMG_TRACED(HMG_K_Z_GREEN, f * 2 * F, launch_z_pass<float>(g, zmode, mask, s->spec32, nullptr, st));
-    HMG_TRACED(HMG_K_Y_INVERSE, f * 2 * F, launch_y_pass<float>(g, false, mask, s->spec32, st));
     if (!last) {
         const bool wtau = b == blk - 2;   // the field the residual sweep compares against
         const double xb = f * 2 * F + (double)g.N3 + (wtau ? f * F : 0.0) + (addr ? f * F : 0.0);
+        if (yxy) {
+            HMG_TRACED(HMG_K_YXY, xb, fast_yxy(g, addr, wtau, mask, s->spec32, s->f32buf, r32in, st));
+            return;
+        }
+        HMG_TRACED(HMG_K_Y_INVERSE, f * 2 * F, launch_y_pass<float>(g, false, mask, s->spec32, st));
         HMG_TRACED(HMG_K_X_ROUND, xb, fast_x_round(g, addr, wtau, mask, s->spec32, s->f32buf, r32in, st));
         return;
     }
+    HMG_TRACED(HMG_K_Y_INVERSE, f * 2 * F, launch_y_pass<float>(g, false, mask, s->spec32, st));
     const double xb = f * 3 * F + (addr ? f * F : 0.0);   // spectrum and old field in, field out
     HMG_TRACED(HMG_K_X_INVERSE, xb,
                launch_x_inverse<float>(g, ximode, mask, s->spec32, s->f32buf, r32in, nullptr, nullptr, pb, st));

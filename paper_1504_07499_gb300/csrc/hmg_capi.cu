@@ -74,11 +74,13 @@ hmg_status prepare(hmg_ctx* ctx, const uint8_t* phase, int N, const double k[3],
         g->nochain = (v >> 2) & 1;
         g->xpers = (v >> 3) & 1;
         g->zpers = (v >> 4) & 1;
+        g->yxy = (v >> 5) & 1;
     }
     if (g->relax != 0.0) {   // relaxed schemes read the old field in every x inverse
         g->xyvar = 0;
         g->nochain = 1;
         g->xpers = 0;
+        g->yxy = 0;
     }
     return HMG_OK;
 }
@@ -149,8 +151,8 @@ size_t hmg_footprint(int N, hmg_precision p) { return state_bytes(N, p == HMG_FP
 
 hmg_status hmg_set_variant(hmg_ctx* ctx, int N, int variant) {
     g_last_error.clear();
-    if (!ctx || !valid_N(N) || variant < -1 || variant > 31) {
-        set_error("bad context, N or variant (-1 .. 31)");
+    if (!ctx || !valid_N(N) || variant < -1 || variant > 63) {
+        set_error("bad context, N or variant (-1 .. 63)");
         return HMG_INVALID_ARG;
     }
     if (variant < 0) ctx->ztune.erase(N);
@@ -531,6 +533,7 @@ static hmg_status fft_common(hmg_ctx* ctx, int N, int count, hmg_precision preci
         g.nochain = (v >> 2) & 1;
         g.xpers = (v >> 3) & 1;
         g.zpers = (v >> 4) & 1;
+        g.yxy = (v >> 5) & 1;
     }
     SolveState& s = ctx->solve;
     const long long N3 = g.N3;

@@ -114,6 +114,7 @@ hmg_status Engine::add(long long id, const uint8_t* phase, int N, const double k
         e->g.nochain = (v >> 2) & 1;
         e->g.xpers = (v >> 3) & 1;
         e->g.zpers = (v >> 4) & 1;
+        e->g.yxy = (v >> 5) & 1;
     }
     launch_init_tau<float>(e->g, 7u, e->st.f32buf, st);
     e->index = (int)entries.size();
@@ -158,12 +159,18 @@ static void block_launches(const Entry* e, int* dflags, cudaStream_t s) {
     if (chain_sweeps(gf)) {
         // chained sweeps: x inverse + next x forward in one kernel, the field stored only
         // before the last sweep (the residual sweep)
+        // (with the plane kernel, the y inverse, x round trip and next y forward are one launch)
+        const bool yxy = gf.yxy && fast_yxy_available(gf);
         launch_x_forward<float>(gf, XF_POLARIZE, 7u, st.f32buf, st.spec32, nullptr, s);
         for (int b = 0; b < kResidualEvery; ++b) {
             const bool last = b == kResidualEvery - 1;
             gf.resid = last;
-            launch_y_pass<float>(gf, true, 7u, st.spec32, s);
+            if (b == 0 || !yxy) launch_y_pass<float>(gf, true, 7u, st.spec32, s);
             launch_z_pass<float>(gf, Z_ITER, 7u, st.spec32, nullptr, s);
+            if (!last && yxy) {
+                fast_yxy(gf, true, b == kResidualEvery - 2, 7u, st.spec32, st.f32buf, st.r32, s);
+                continue;
+            }
             launch_y_pass<float>(gf, false, 7u, st.spec32, s);
             if (!last)
                 fast_x_round(gf, true, b == kResidualEvery - 2, 7u, st.spec32, st.f32buf, st.r32, s);

@@ -822,6 +822,112 @@ k_fx_round_p(GridDesc g, unsigned mask, float2* __restrict__ spec, float* __rest
     }
 }
 
+// ---------------------------------------------------------------------------
+// y inverse + x round trip + y forward of a (component, z) plane in one persistent kernel.
+// A CTA takes whole planes: it transforms the plane's columns along y in place, then its
+// rows (x inverse, update, polarization of the next sweep, x forward), then its columns
+// again, the plane (N x N/2 complex values) staying in L2 between the three phases, so a
+// sweep makes two HBM round trips (this pass and the z pass) instead of four.  Each phase
+// runs the operations of the separate kernels (k_fy, k_fx_round, k_fy) on the same data.
+// The spectrum pointer is not __restrict__: each phase reads what other threads of the CTA
+// wrote in the phase before (ordered by the CTA barriers), so no load may take the
+// read-only path.
+// ---------------------------------------------------------------------------
+
+template <int L>
+struct YxyShape {
+    static constexpr int M = L / 2;
+    static constexpr int P = 256 / Split<L>::TP;        // columns per y step
+    static constexpr int RW = 256 / Split<M>::TP;       // rows per x step
+    static constexpr int SY = P * xslots<L>();
+    static constexpr int SX = RW * row_stride<M>();
+    static constexpr size_t smem = sizeof(float2) * (SY > SX ? SY : SX);
+};
+
+// P columns of a plane along y (threads (p, t), p fastest), transformed in place.
+template <int L, int P, bool FWD>
+__device__ __forceinline__ void y_columns(const GridDesc& g, float2* base, int t, float2* sh) {
+    constexpr int E = Split<L>::E, TP = Split<L>::TP, KPT = E / TP, M = L / 2;
+    float2 v[E];
+#pragma unroll
+    for (int n1 = 0; n1 < E; ++n1) v[n1] = base[(long long)(TP * n1 + t) * M];
+    const float2* twL = g.tw32 + g.pN.tw_off;
+    stage1_write<L, FWD>(v, t, twL, sh, P);
+    __syncthreads();
+    stage2_read<L, FWD>(v, t, sh, P);
+#pragma unroll
+    for (int i = 0; i < KPT; ++i)
+#pragma unroll
+        for (int k2 = 0; k2 < TP; ++k2) base[(long long)(t * KPT + i + E * k2) * M] = v[i * TP + k2];
+}
+
+template <int L, bool ADDR, bool WTAU>
+__global__ void __launch_bounds__(256, 2)
+k_yxy(GridDesc g, unsigned mask, float2* spec, float* __restrict__ tau, const float* __restrict__ r32, int nper) {
+    using S = YxyShape<L>;
+    constexpr int M = S::M, P = S::P, RW = S::RW;
+    constexpr int N = L;
+    constexpr int EX = Split<M>::E, TPX = Split<M>::TP, RS = row_stride<M>();
+    extern __shared__ __align__(16) float2 sh[];
+    __shared__ float2 lut[16];
+    __shared__ float2 tws[2 * M];
+    coef_pairs(lut, (float)g.Y[0], (float)g.Y[1], (float)g.Y[2]);
+    stage_twiddles<M>(tws, g);
+    __syncthreads();
+    const float2* twM = tws;
+    const float2* twN = tws + M;
+    const int nitems = g.nslots * nper;
+    for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
+        const int slot = item / nper, pz = item % nper;   // pz = component * N + z
+        if (!slot_active(g, mask, slot)) continue;         // uniform over the CTA
+        float2* plane = spec + (long long)slot * 3 * g.NNM + (long long)pz * N * M;
+        // y inverse (step 5, first axis), columns in place
+        {
+            const int p = threadIdx.x % P, t = threadIdx.x / P;
+            for (int kb = 0; kb < M / P; ++kb) {
+                y_columns<L, P, false>(g, plane + kb * P + p, t, sh + p);
+                __syncthreads();
+            }
+        }
+        // x inverse, update (step 7), optional store, polarization (step 2), x forward (step 3)
+        {
+            const int t = threadIdx.x % TPX, r = threadIdx.x / TPX;
+            const bool addr = ADDR && (g.dflags ? (g.dflags[slot] & SF_ADDR) != 0 : true);
+            float2* rs = sh + r * RS;
+            for (int rb = 0; rb < N / RW; ++rb) {
+                const int y = rb * RW + r;
+                const long long row = (long long)pz * N + y;                   // c*NN + z*N + y
+                const long long fbase = (long long)slot * 3 * g.N3 + row * N;
+                float2 radd[EX];
+                if (addr) s2_load<M>(radd, reinterpret_cast<const float2*>(r32 + fbase), t);
+                uchar2 q[EX];
+                s2_load_phase<M>(q, reinterpret_cast<const uchar2*>(g.phase + (row % g.NN) * N), t);
+                float2* sp = plane + (long long)y * M;
+                float2 v[EX];
+                row_inverse<M, TPX, EX>(v, t, rs, sp, twM, twN);
+#pragma unroll
+                for (int j = 0; j < EX; ++j)
+                    if (addr) v[j] = make_float2(__fadd_rn(v[j].x, radd[j].x), __fadd_rn(v[j].y, radd[j].y));
+                if (WTAU) s2_store<M>(reinterpret_cast<float2*>(tau + fbase), v, t);
+#pragma unroll
+                for (int j = 0; j < EX; ++j) v[j] = __fmul2_rn(v[j], lut[pair_index(q[j])]);
+                row_sync<TPX>();
+                row_forward_split<M, TPX, EX>(v, t, rs, twM, twN, sp);
+                row_sync<TPX>();
+            }
+        }
+        __syncthreads();   // the rows are in memory; the exchange buffer takes the columns
+        // y forward (step 3, second axis) of the next sweep, columns in place
+        {
+            const int p = threadIdx.x % P, t = threadIdx.x / P;
+            for (int kb = 0; kb < M / P; ++kb) {
+                y_columns<L, P, true>(g, plane + kb * P + p, t, sh + p);
+                __syncthreads();
+            }
+        }
+    }
+}
+
 }  // namespace fast
 
 // ---------------------------------------------------------------------------
@@ -1168,6 +1274,42 @@ bool fast_x_round(const GridDesc& g, bool addr, bool wtau, unsigned mask, void* 
         default: return false;
     }
 #undef FXR
+}
+
+namespace {
+template <int L, bool ADDR, bool WTAU>
+void launch_yxy(const GridDesc& g, unsigned mask, float2* sp, float* tau, const float* r32, cudaStream_t st) {
+    auto kern = fast::k_yxy<L, ADDR, WTAU>;
+    constexpr size_t sm = fast::YxyShape<L>::smem;
+    const int nper = 3 * g.N;
+    const int grid = persistent_grid(kern, 256, sm, nper * g.nslots);
+    kern<<<grid, 256, sm, st>>>(g, mask, sp, tau, r32, nper);
+}
+}  // namespace
+
+bool fast_yxy_available(const GridDesc& g) {
+    return g.relax == 0.0 && (g.N == 64 || g.N == 128 || g.N == 192 || g.N == 256);
+}
+
+bool fast_yxy(const GridDesc& g, bool addr, bool wtau, unsigned mask, void* spec, float* tau, const float* r32,
+              cudaStream_t st) {
+    if (!fast_yxy_available(g)) return false;
+    float2* sp = reinterpret_cast<float2*>(spec);
+#define FYXY(L)                                                                        \
+    {                                                                                  \
+        if (addr && wtau) launch_yxy<L, true, true>(g, mask, sp, tau, r32, st);        \
+        else if (addr) launch_yxy<L, true, false>(g, mask, sp, tau, r32, st);          \
+        else if (wtau) launch_yxy<L, false, true>(g, mask, sp, tau, r32, st);          \
+        else launch_yxy<L, false, false>(g, mask, sp, tau, r32, st);                   \
+    }
+    switch (g.N) {
+        HMG_FAST_LEN(64, FYXY)
+        HMG_FAST_LEN(128, FYXY)
+        HMG_FAST_LEN(192, FYXY)
+        HMG_FAST_LEN(256, FYXY)
+        default: return false;
+    }
+#undef FYXY
 }
 
 #undef HMG_FAST_LEN

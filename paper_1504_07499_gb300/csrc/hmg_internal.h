@@ -53,6 +53,8 @@ struct GridDesc {
     int nochain;           // 1: FP32 sweeps of a block are not chained through k_fx_round
     int xpers;             // 1: the chained x round trip runs as a persistent kernel that
                            //    stages its next rows with bulk copies (autotuned)
+    int yxy;               // 1: the chained sweeps' y inverse, x round trip and y forward run
+                           //    as one persistent kernel per (component, z) plane (autotuned)
     int zpers;             // 1: the z pass of plain and correction sweeps runs as a
                            //    persistent kernel that stages its next columns with tiled
                            //    tensor copies (autotuned)
@@ -121,6 +123,11 @@ bool fast_x_round(const GridDesc& g, bool addr, bool wtau, unsigned mask, void* 
 // FP32 sweeps of a block are chained (x inverse + next x forward in one kernel):
 // register-resident x kernels exist for g.N, separate x and y passes, chaining not off.
 bool chain_sweeps(const GridDesc& g);
+// y inverse + x round trip + y forward of each plane in one persistent kernel (sizes 64,
+// 128, 192, 256; not for relaxed schemes); false when it does not apply.
+bool fast_yxy_available(const GridDesc& g);
+bool fast_yxy(const GridDesc& g, bool addr, bool wtau, unsigned mask, void* spec, float* tau, const float* r32,
+              cudaStream_t st);
 // True (and cleared) when a persistent kernel's bounded wait for a bulk copy gave up
 // since the last call; the results of that launch are invalid.
 bool fast_take_wait_failure();

@@ -35,7 +35,7 @@ EXPORTS = ["hmg_version", "hmg_last_error", "hmg_create", "hmg_destroy", "hmg_vo
            "hmg_submit_rve", "hmg_fp64_rate", "hmg_voxelize_mixed"]
 HMG_NOALLOC_MAX_N = 64
 KERNEL_KINDS = ["x_forward", "y_forward", "z_green", "y_inverse", "x_inverse", "eq_x", "eq_z", "other",
-                "x_round", "fp64"]
+                "x_round", "fp64", "yxy"]
 
 
 class hmg_sphere(C.Structure):

@@ -87,19 +87,21 @@ def test_benchmark_rve_eight_chained_sweeps_every_voxel(ctx, N):
 
 @pytest.mark.parametrize("N", [192, 256])
 def test_benchmark_rve_x_round_forms_bit_identical(ctx, N):
-    """Eight chained sweeps on the benchmark RVE with the plain kernels and with the
-    persistent x round trip and z pass (variant bits 3 and 4): the same fields, bit for bit."""
+    """Eight chained sweeps on the benchmark RVE with the plain kernels, with the
+    persistent x round trip and z pass (variant bits 3 and 4) and with the plane kernel
+    (bit 5: y inverse, x round trip and y forward in one launch): the same fields, bit for
+    bit."""
     sl = I.generate_spheres(3000, 100, 0.40)
     ph = ctx.voxelize(sl.spheres, 0.3, N)
     fields = []
-    for v in (0, 8, 24):
+    for v in (0, 8, 24, 56):
         hmg.hmg_set_variant(ctx.handle, N, v)
         e = torch.empty((3, 3, N, N, N), dtype=torch.float64, device="cuda")
         hmg.hmg_solve_fields(ctx.handle, ph, N, K3, 1e-8, hmg.HMG_FP32_BULK, e, max_iter=8,
                              allow=(hmg.HMG_NOT_CONVERGED,))
         fields.append(e)
     hmg.hmg_set_variant(ctx.handle, N, -1)
-    assert torch.equal(fields[0], fields[1]) and torch.equal(fields[0], fields[2])
+    assert all(torch.equal(fields[0], f) for f in fields[1:])
 
 
 @pytest.mark.parametrize("prec,tol,iters_exact", [(hmg.HMG_FP32_BULK, 1e-5, False), (hmg.HMG_FP64, 1e-9, True)])

@@ -119,7 +119,7 @@ def test_autotuner_records_a_variant(ctx):
     e[0] = 1.0
     hmg.hmg_em_iterate(ctx.handle, ph, N, K3, (1.0, 0.0, 0.0), hmg.HMG_FP32_BULK, 1, e)
     v = hmg.hmg_get_variant(ctx.handle, N)
-    assert 0 <= v < 32 and not (v & 4)            # bits 0, 1, 3, 4 chosen; chaining kept on
+    assert 0 <= v < 64 and not (v & 4)            # bits 0, 1, 3, 4, 5 chosen; chaining kept on
 
 
 @pytest.mark.parametrize("N", [64, 96, 128])
@@ -180,6 +180,49 @@ def test_persistent_kernels_are_bit_identical(ctx, N, pers):
     assert np.array_equal(out[0][0], out[1][0])
     assert list(out[0][1]["iters"]) == list(out[1][1]["iters"])
     assert np.array_equal(out[0][2], out[1][2])
+
+
+@pytest.mark.parametrize("N,base", [(64, 0), (128, 0), (128, 16), (192, 0), (192, 16)])
+def test_plane_kernel_is_bit_identical(ctx, N, base):
+    """Chained sweeps with the plane kernel (variant bit 5: the y inverse, the x round trip
+    and the next sweep's y forward of each (component, z) plane in one persistent launch)
+    against the separate passes: the same K, sweep counts and fields, bit for bit,
+    correction sweeps (r added) and the stored field of the residual sweep included."""
+    sl = I.generate_spheres(1000, 30, 0.2)
+    ph = om.voxelize(sl.spheres, 0.3, N)
+    k = (0.20, 0.25, 40.0)
+    out = []
+    for v in (base, base | 32):
+        hmg.hmg_set_variant(ctx.handle, N, v)
+        e = np.empty((3, 3, N, N, N))
+        K, info, st = hmg.hmg_solve_fields(ctx.handle, ph, N, k, 1e-8, hmg.HMG_FP32_BULK, e)
+        assert st == hmg.HMG_OK
+        assert info["fp64_rounds"] > 0          # correction sweeps ran
+        out.append((K, info, e))
+    hmg.hmg_set_variant(ctx.handle, N, -1)
+    assert np.array_equal(out[0][0], out[1][0])
+    assert list(out[0][1]["iters"]) == list(out[1][1]["iters"])
+    assert np.array_equal(out[0][2], out[1][2])
+
+
+def test_plane_kernel_in_the_batch_engine_is_bit_identical(ctx):
+    """The many-RVE engine's chained blocks (per-slot flags, correction sweeps, one graph
+    per round) with and without the plane kernel: the same K and sweep counts."""
+    Ns = [64, 128, 64, 128, 64]
+    phases = [om.voxelize(I.generate_spheres(40 + i, 25, 0.2).spheres, 0.3, N) for i, N in enumerate(Ns)]
+    res = []
+    for v in (0, 32):
+        for N in (64, 128):
+            hmg.hmg_set_variant(ctx.handle, N, v)
+        K, infos, st = hmg.hmg_solve_batch(ctx.handle, phases, Ns, np.tile((0.20, 0.25, 40.0), (len(Ns), 1)),
+                                           1e-8, hmg.HMG_FP32_BULK)
+        assert st == hmg.HMG_OK
+        res.append((K, infos))
+    for N in (64, 128):
+        hmg.hmg_set_variant(ctx.handle, N, -1)
+    assert np.array_equal(res[0][0], res[1][0])
+    for a, b in zip(res[0][1], res[1][1]):
+        assert list(a["iters"]) == list(b["iters"])
 
 
 def test_autotuner_choices_persist_on_disk(tmp_path):
