@@ -711,6 +711,7 @@ hmg_status Solver::run_bulk(int max_iter, double tol, hmg_info* info, double K[9
     int state[3], iters[3] = {0, 0, 0}, it64[3] = {0, 0, 0}, status[3];
     double eps_comp[3] = {INFINITY, INFINITY, INFINITY}, eps_eq[3] = {INFINITY, INFINITY, INFINITY};
     double eps32[3] = {INFINITY, INFINITY, INFINITY}, best[3], outer_eps[3] = {INFINITY, INFINITY, INFINITY};
+    double qeq[3];   // the ratio eps_eq / eps_comp the correction solves aim for
     int since_best[3] = {0, 0, 0};
     double flux[3][3] = {};
     int rounds = 0;
@@ -719,7 +720,9 @@ hmg_status Solver::run_bulk(int max_iter, double tol, hmg_info* info, double K[9
         status[sl] = HMG_NOT_CONVERGED;
         best[sl] = INFINITY;
     }
-    const double thetaA = std::max(tol, 1e-6);
+    const bool em = g.scheme == HMG_SCHEME_EYRE_MILTON && g.relax == 0.0;
+    const double thetaA = std::max(tol, em ? kBulkExit : kBulkExitSlow);
+    for (int sl = 0; sl < 3; ++sl) qeq[sl] = em ? kEqRatio0 : kEqRatio0Slow;
     const double eta = 1e-4;           // inner solves reduce the outer residual by this factor
     const int stall = 24;              // sweeps without a new best residual = FP32 floor
     // a new best must improve by this factor; the basic scheme contracts by only
@@ -787,6 +790,9 @@ hmg_status Solver::run_bulk(int max_iter, double tol, hmg_info* info, double K[9
                 status[sl] = HMG_OK;
                 state[sl] = PH_DONE;
             } else {
+                // the test ran on the iterate whose FP64 sweep gave eps_comp: aim the next
+                // correction solve at the ratio it measured
+                if (eps_comp[sl] > 0.0) qeq[sl] = std::max(qeq[sl], eps_eq[sl] / eps_comp[sl]);
                 state[sl] = PH_INNER;
                 best[sl] = INFINITY;
                 since_best[sl] = 0;
@@ -833,7 +839,7 @@ hmg_status Solver::run_bulk(int max_iter, double tol, hmg_info* info, double K[9
             if (a) {
                 eps_comp[sl] = eps32[sl];
                 if (eps32[sl] < thetaA || since_best[sl] >= stall) to_outer_a |= 1u << sl;
-            } else if (eps32[sl] < std::max(eta * outer_eps[sl], kInnerFloor * tol) || since_best[sl] >= stall) {
+            } else if (eps32[sl] < std::max(eta * outer_eps[sl], inner_target(tol, qeq[sl])) || since_best[sl] >= stall) {
                 to_outer_i |= 1u << sl;
             }
         }

@@ -316,6 +316,7 @@ hmg_status Engine::tick_launch_and_update() {
                     m.status = HMG_OK;
                     m.state = PH_DONE;
                 } else {
+                    if (m.eps_comp > 0.0) m.qeq = std::max(m.qeq, m.eps_eq / m.eps_comp);
                     m.state = PH_INNER;
                     m.best = INFINITY;
                     m.since_best = 0;
@@ -360,8 +361,8 @@ hmg_status Engine::tick_launch_and_update() {
             }
             if (fl & SF_ADDB) {   // plain phase
                 m.eps_comp = m.eps32;
-                if (m.eps32 < std::max(e->tol, 1e-6) || m.since_best >= kStall) to_a |= 1u << sl;
-            } else if (m.eps32 < std::max(kEta * m.outer_eps, kInnerFloor * e->tol) || m.since_best >= kStall) {
+                if (m.eps32 < std::max(e->tol, kBulkExit) || m.since_best >= kStall) to_a |= 1u << sl;
+            } else if (m.eps32 < std::max(kEta * m.outer_eps, inner_target(e->tol, m.qeq)) || m.since_best >= kStall) {
                 to_i |= 1u << sl;
             }
         }

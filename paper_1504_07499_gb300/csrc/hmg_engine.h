@@ -30,6 +30,7 @@ struct SlotSM {
     int iters = 0, it64 = 0, since_best = 0;
     double eps_comp = INFINITY, eps_eq = INFINITY, eps32 = INFINITY, best = INFINITY, outer_eps = INFINITY;
     double flux[3] = {0, 0, 0};
+    double qeq = kEqRatio0;   // the ratio eps_eq / eps_comp the correction solves aim for
 };
 
 struct Entry {

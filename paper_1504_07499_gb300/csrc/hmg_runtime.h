@@ -100,10 +100,29 @@ struct Tracer {
 // block computes the residual and the host reads it once per block.
 constexpr int kResidualEvery = 4;
 
-// A correction solve stops once its residual is below this fraction of the tolerance:
-// the FP64 residual that follows is then below tol, and reducing it further only costs
-// sweeps (the tolerance itself is checked in FP64).
-constexpr double kInnerFloor = 0.1;
+// Hand-over between the phases of an FP32-bulk solve (per gradient).
+// The solve stops on the FP64 equilibrium test (step 1), and at the end of a correction
+// solve eps_eq is a steady multiple q of eps_comp (on the 256^3 benchmark RVE q = 3 at
+// contrast 10, 8 at 200, 18-20 at 2000 and 25-33 at 20000), so a correction solve stops
+// once its residual is below tol / (kEqMargin q).  q starts at kEqRatio0; after an
+// equilibrium test that fails it becomes the ratio that test measured, so the next
+// correction solve is aimed at the tolerance instead of creeping towards it one block of
+// sweeps (and two FP64 passes) at a time.
+constexpr double kEqRatio0 = 20.0;
+constexpr double kEqMargin = 1.25;
+// The basic and relaxed schemes start from a stop at 0.1 tol.
+constexpr double kEqRatio0Slow = 8.0;
+
+// The plain FP32 sweeps of an Eyre-Milton solve hand over to the FP64 correction once their
+// residual is below this (or the tolerance, if larger): above the FP32 floor of a
+// contrast-2000 solve (about 1.2e-6), so no sweeps are spent on the floor waiting for the
+// stall test.  The basic and relaxed schemes, whose correction solves are limited by the
+// FP32 noise of their slow contraction, keep the deeper hand-over.
+constexpr double kBulkExit = 3e-6;
+constexpr double kBulkExitSlow = 1e-6;
+
+// Stop of a correction solve for a gradient whose ratio eps_eq / eps_comp is taken as q.
+inline double inner_target(double tol, double q) { return tol / (kEqMargin * q); }
 
 // Driver of one solve on one SolveState.
 struct Solver {
