@@ -719,13 +719,15 @@ k_fx_round(GridDesc g, unsigned mask, float2* __restrict__ spec, float* __restri
 
 // Dynamic shared memory of k_fx_round_p: the staged spectrum rows of one block (each
 // row padded by 64 bytes, so that the two rows a half-warp reads fall on different bank
-// halves), the block's phase rows, and the rows' exchange buffers.
+// halves), the block's phase rows (each padded by 32 bytes, so that the rows of a warp
+// read different banks), and the rows' exchange buffers.
 template <int M, int RW>
 struct RoundSmem {
     static constexpr int SROW = M + 8;
+    static constexpr int PROW = 2 * M + 32;
     static constexpr size_t spec_bytes = (size_t)RW * SROW * sizeof(float2);
     static constexpr size_t phase_off = spec_bytes;
-    static constexpr size_t phase_bytes = (size_t)RW * 2 * M;
+    static constexpr size_t phase_bytes = (size_t)RW * PROW;
     static constexpr size_t x_off = (phase_off + phase_bytes + 15) / 16 * 16;
     static constexpr size_t total = x_off + (size_t)RW * row_stride<M>() * sizeof(float2);
 };
@@ -768,7 +770,9 @@ k_fx_round_p(GridDesc g, unsigned mask, float2* __restrict__ spec, float* __rest
         async::mbar_expect(mb, (uint32_t)(RW * M * sizeof(float2) + RW * N));
         for (int rr = 0; rr < RW; ++rr)
             async::bulk_g2s(async::smem_addr(sspec + rr * L::SROW), src + (long long)rr * M, M * sizeof(float2), mb);
-        async::bulk_g2s(async::smem_addr(sphase), g.phase + (long long)(b / 3) * RW * N, RW * N, mb);
+        const uint8_t* prow = g.phase + (long long)(b / 3) * RW * N;
+        for (int rr = 0; rr < RW; ++rr)
+            async::bulk_g2s(async::smem_addr(sphase + rr * L::PROW), prow + (long long)rr * N, N, mb);
     };
     if (threadIdx.x == 0) issue(item);
     __syncthreads();   // barrier initialized, tables staged
@@ -796,7 +800,7 @@ k_fx_round_p(GridDesc g, unsigned mask, float2* __restrict__ spec, float* __rest
 #pragma unroll
         for (int n1 = 0; n1 < E; ++n1) xk[n1] = sspec[r * L::SROW + TP * n1 + t];
         uchar2 q[E];
-        s2_load_phase<M>(q, reinterpret_cast<const uchar2*>(sphase + r * N), t);
+        s2_load_phase<M>(q, reinterpret_cast<const uchar2*>(sphase + r * L::PROW), t);
         __syncthreads();   // every thread holds its rows: the buffers take the next block
         int nxt = item + gridDim.x;
         while (nxt < nitems && !slot_active(g, mask, nxt / nblk)) nxt += gridDim.x;

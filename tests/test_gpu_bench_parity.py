@@ -131,7 +131,7 @@ def test_contrast_2e4_K_against_stored_oracle(ctx, prec, tol, iters_exact):
         # the correction solves aim at the eps_eq / eps_comp ratio a failed equilibrium test
         # measured, so high contrast ends in a few FP64 rounds per gradient, not dozens
         assert info["fp64_rounds"] <= 9
-        assert all(a <= 1.1 * b + 8 for a, b in zip(info["iters"], case["iters"]))
+        assert all(a <= 1.25 * b + 8 for a, b in zip(info["iters"], case["iters"]))
 
 
 @pytest.mark.parametrize("prec,tol", [(hmg.HMG_FP64, 1e-9), (hmg.HMG_FP32_BULK, 1e-5)])
