@@ -339,7 +339,9 @@ int autotune_z(::hmg_ctx* c, GridDesc g, SolveState* s, cudaStream_t st) {
                 launch_y_pass<float>(g, true, all, s->spec32, st);
             }, 4);
         }
-        yxybest = yms[1] < yms[0] ? 1 : 0;
+        // measured within a few per cent of the separate passes at 256^3: taken only when it
+        // wins clearly, so that timing noise does not flip the choice from context to context
+        yxybest = yms[1] < 0.97f * yms[0] ? 1 : 0;
         if (fast_take_wait_failure()) yxybest = 0;
     }
     cudaGetLastError();
