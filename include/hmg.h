@@ -372,7 +372,9 @@ hmg_status hmg_poll(hmg_ctx* ctx, uint64_t ticket, double K_out[9], hmg_info* in
  *          x round trip and the y forward of the next sweep run as one persistent kernel
  *          whose CTAs take whole (component, z) planes, so that each plane stays in L2
  *          between the three passes (bit-identical results; bit 3 then has no effect).
- * The autotuner chooses bits 0, 1, 3, 4 and 5 and leaves bit 2 clear.  hmg_set_variant pins
+ * The autotuner chooses bits 0, 1, 3 and 4 and leaves bits 2 and 5 clear (the plane kernel
+ * times faster alone than the passes it replaces but is even with them inside a solve).
+ * hmg_set_variant pins
  * `variant` (0 .. 63) for size N, or clears the choice (-1) so that the next solve
  * times them again.  All give the same results to rounding.
  * When the environment variable HMG_TUNE_CACHE names a file, a context takes the choice

@@ -323,29 +323,10 @@ int autotune_z(::hmg_ctx* c, GridDesc g, SolveState* s, cudaStream_t st) {
         xpbest = xms[1] < xms[0] ? 1 : 0;
         if (fast_take_wait_failure()) xpbest = 0;
     }
-    // y inverse + x round trip + y forward: separate passes or the plane kernel
-    int yxybest = 0;
-    g.xpers = xpbest;
-    if (chain_sweeps(g) && fast_yxy_available(g)) {
-        float yms[2];
-        for (int v = 0; v < 2; ++v) {
-            yms[v] = time_launches(st, [&] {
-                if (v == 1) {
-                    fast_yxy(g, false, false, all, s->spec32, s->f32buf, nullptr, st);
-                    return;
-                }
-                launch_y_pass<float>(g, false, all, s->spec32, st);
-                fast_x_round(g, false, false, all, s->spec32, s->f32buf, nullptr, st);
-                launch_y_pass<float>(g, true, all, s->spec32, st);
-            }, 4);
-        }
-        // measured within a few per cent of the separate passes at 256^3: taken only when it
-        // wins clearly, so that timing noise does not flip the choice from context to context
-        yxybest = yms[1] < 0.97f * yms[0] ? 1 : 0;
-        if (fast_take_wait_failure()) yxybest = 0;
-    }
     cudaGetLastError();
-    best = zbest | (xybest << 1) | (xpbest << 3) | (zpbest << 4) | (yxybest << 5);
+    // bit 5 (the plane kernel) is not timed here: alone it times a few per cent faster than
+    // the three passes it replaces, inside a solve it is even, so it is left to hmg_set_variant
+    best = zbest | (xybest << 1) | (xpbest << 3) | (zpbest << 4);
     c->ztune[g.N] = best;
     tune_cache_write(c->device, g.N, best);
     return best;

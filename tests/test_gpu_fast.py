@@ -119,7 +119,7 @@ def test_autotuner_records_a_variant(ctx):
     e[0] = 1.0
     hmg.hmg_em_iterate(ctx.handle, ph, N, K3, (1.0, 0.0, 0.0), hmg.HMG_FP32_BULK, 1, e)
     v = hmg.hmg_get_variant(ctx.handle, N)
-    assert 0 <= v < 64 and not (v & 4)            # bits 0, 1, 3, 4, 5 chosen; chaining kept on
+    assert 0 <= v < 32 and not (v & 4)            # bits 0, 1, 3, 4 chosen; chaining kept on
 
 
 @pytest.mark.parametrize("N", [64, 96, 128])
